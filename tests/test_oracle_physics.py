@@ -1,0 +1,262 @@
+"""Pins of the FP64 oracle's time stepping against what the paper and textbook
+physics fix (CPU only).
+
+* isotropic stencils (Eqs. 41-42) are exact on quadratic fields; mirror ghosts
+* exact conservation of sum(phi) and sum(c1 + c2) (Sec. IV B 1 states that the
+  total scalar content is conserved; sum F_i = 0 keeps sum phi)
+* the tanh profile of Eq. (2) is a stationary solution of Eq. (1), up to a
+  second-order discretisation error in dx/W
+* Laplace's law dp = sigma / R for a static 2D droplet
+* the erfc solution of two semi-infinite phases with a Henry jump (Eqs. 8, 9, 12)
+* the flat equilibrium of Sec. IV A 2 (c1 + K c2 flat; printed level 1 for
+  D1 = D2 = K = 1)
+* the pseudo-single-phase case of Sec. IV A 1 (heat kernel)
+* Poiseuille flow u_max = G H^2 / (8 mu) for the three viscosity relations
+* mirror/transpose symmetry of a centred droplet (catches swapped x/y terms)
+"""
+import json
+import os
+from math import erfc, sqrt
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_15752_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tanh_phi(sdf, W):
+    return 0.5 + 0.5 * np.tanh(2.0 * sdf / W)
+
+
+# ------------------------------------------------------------- stencils ----
+def test_stencils_exact_on_quadratics():
+    nx, ny = 12, 10
+    x, y = wl.grid(nx, ny)
+    g = np.random.Generator(np.random.PCG64(3))
+    a = g.normal(size=6)
+    q = a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y
+    s = oracle.OracleSim(dict(nx=nx, ny=ny, wall_x=1, wall_y=1, A=0.0))
+    s.init_fields(q, 0.5 * q, 0.25 * q)
+    st = s.stencils()
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    gx = a[1] + 2 * a[3] * x + a[4] * y
+    gy = a[2] + a[4] * x + 2 * a[5] * y
+    lap = 2 * a[3] + 2 * a[5]
+    assert np.allclose(st["dphix"][inner], gx[inner], atol=1e-10)
+    assert np.allclose(st["dphiy"][inner], gy[inner], atol=1e-10)
+    assert np.allclose(st["lap"][inner], lap, atol=1e-10)
+    # the scalars were initialised to multiples of the same field
+    assert np.allclose(st["dc1x"][inner], 0.5 * gx[inner], atol=1e-10)
+    assert np.allclose(st["dc2y"][inner], 0.25 * gy[inner], atol=1e-10)
+
+
+def test_wall_stencil_sees_mirror_ghosts():
+    nx, ny = 6, 5
+    x, _ = wl.grid(nx, ny)
+    s = oracle.OracleSim(dict(nx=nx, ny=ny, wall_x=1, wall_y=0, A=0.0))
+    s.init_fields(x, 0 * x, 0 * x)
+    st = s.stencils()
+    # ghost at x = -1 equals phi(0) = 0: grad_x = 3 [1/9 (1 - 0) + 2/36 (1 - 0)] = 1/2
+    assert np.allclose(st["dphix"][:, 0], 0.5, atol=1e-14)
+    assert np.allclose(st["dphix"][:, 1:-1], 1.0, atol=1e-14)
+    assert np.allclose(st["dphix"][:, -1], 0.5, atol=1e-14)
+    assert np.allclose(st["dphiy"], 0.0, atol=1e-14)
+    # lap at x = 0: 6 [1/9 (1 - 0) + 2/36 (1 - 0)] = 1 ; at x = nx-1 the mirror gives -1
+    assert np.allclose(st["lap"][:, 0], 1.0, atol=1e-13)
+    assert np.allclose(st["lap"][:, -1], -1.0, atol=1e-13)
+
+
+# --------------------------------------------------------- init / moments --
+def test_init_returns_the_given_macros():
+    w = wl.droplet64(nx=24, ny=20, R=6.0)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, 1.0, 0.3)
+    f = s.fields()
+    phi = tanh_phi(w.sdf, w.params["W"])
+    assert np.allclose(f["phi"], phi, atol=1e-15, rtol=0)
+    assert np.allclose(f["c1"], phi, atol=1e-14, rtol=0)
+    assert np.allclose(f["c2"], 0.3 * (1 - phi), atol=1e-14, rtol=0)
+
+
+# ---------------------------------------------------------- conservation --
+@pytest.mark.parametrize("case", ["droplet_periodic", "bubble_walls"])
+def test_total_phase_and_scalar_are_conserved(case):
+    if case == "droplet_periodic":
+        w = wl.droplet64(nx=40, ny=36, R=10.0)
+    else:
+        w = wl.bubble1024x2048(nx=32, ny=64, R=8.0, gy=-1e-5)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+    c0 = s.conserved()
+    s.step(500)
+    c1 = s.conserved()
+    assert np.all(np.isfinite(c1))
+    assert abs(c1[0] - c0[0]) / c0[0] < 1e-12
+    assert abs(c1[1] - c0[1]) / c0[1] < 1e-12
+    # the bubble moved: the test is not vacuous
+    if case == "bubble_walls":
+        f = s.fields()
+        assert np.abs(f["uy"]).max() > 1e-6
+
+
+# ------------------------------------------------------- tanh equilibrium --
+def _tanh_deviation(W, steps=1000):
+    nx = 128
+    p = dict(wl.BASE, nx=nx, ny=1, wall_x=1, sigma=0.0, W=W)
+    sdf = wl.sdf_planar_x(nx, 1, 64.0)
+    s = oracle.OracleSim(p)
+    s.init(sdf, 1.0, 0.0)
+    phi0 = s.fields()["phi"]
+    s.step(steps)
+    return np.abs(s.fields()["phi"] - phi0).max()
+
+
+def test_tanh_profile_is_stationary_to_second_order():
+    d4, d8 = _tanh_deviation(4.0), _tanh_deviation(8.0)
+    assert d8 < 3e-3
+    assert d4 < 1e-2
+    # second order in dx/W: halving dx/W divides the deviation by about 4
+    assert 2.5 < d4 / d8 < 5.0
+
+
+# ----------------------------------------------------------- Laplace law --
+@pytest.mark.parametrize("R", [8.0, 16.0])
+def test_laplace_law(R):
+    n = int(4 * R)
+    w = wl.droplet64(nx=n, ny=n, R=R)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, 1.0, 0.0)
+    s.step(4000)
+    f = s.fields()
+    phi, p = f["phi"], f["p"]
+    dp = p[phi > 0.99].mean() - p[phi < 0.01].mean()
+    R_eff = sqrt(phi.sum() / np.pi)
+    assert dp * R_eff / w.params["sigma"] == pytest.approx(1.0, abs=0.05)
+
+
+# ------------------------------------------------------------------ erfc --
+def test_planar_interface_matches_erfc_solution():
+    nx, steps = 512, 5000
+    w = wl.planar1024(nx=nx, ny=1, steps=steps)
+    p = w.params
+    s = oracle.OracleSim(p)
+    s.init(w.sdf, 1.0, 0.0)
+    s.step(steps)
+    f = s.fields()
+    x0, D1, D2, K = nx / 2, p["D1"], p["D2"], p["Keq"]
+    r = sqrt(D2 / D1)
+    x = np.arange(nx)
+    phi, c1, c2 = f["phi"][0], f["c1"][0], f["c2"][0]
+    errs = []
+    for i in range(nx):
+        d = x[i] - x0
+        if d < -3 * p["W"]:
+            exact = 1 - r / (K + r) * erfc((x0 - x[i]) / (2 * sqrt(D1 * steps)))
+            errs.append(abs(c1[i] / phi[i] - exact))
+        elif d > 3 * p["W"]:
+            exact = 1 / (K + r) * erfc((x[i] - x0) / (2 * sqrt(D2 * steps)))
+            errs.append(abs(c2[i] / (1 - phi[i]) - exact))
+    assert len(errs) > 400
+    assert max(errs) < 0.01
+    # the jump is really there: phase-1 side near the interface is well below 1
+    assert c1[int(x0) - 13] / phi[int(x0) - 13] < 0.99
+
+
+# ------------------------------------------------------- flat equilibrium --
+def test_flat_equilibrium_of_sec_iv_a2():
+    g = json.load(open(os.path.join(GOLDEN, "flat_equilibrium.json")))
+    N = 100  # half the paper's resolution keeps the run short; W = 4 dx as in the paper
+    dx = (g["domain"]["x_max"] - g["domain"]["x_min"]) / N
+    xs = g["domain"]["x_min"] + dx * np.arange(N)
+    sdf = (-(xs - 0.5) * (xs + 0.5)) / dx
+    levels = []
+    for case in g["cases"]:
+        Dmax = max(case["D1"], case["D2"])
+        # diffusivities scaled to lattice units keeping D1/D2; A in 1/length^2
+        p = dict(wl.BASE, nx=N, ny=1, D1=0.2 * case["D1"] / Dmax, D2=0.2 * case["D2"] / Dmax,
+                 Keq=case["Keq"], A=g["fixed"]["A"] * dx * dx)
+        phi = tanh_phi(sdf, 4.0)
+        s = oracle.OracleSim(p)
+        s.init_fields(phi[None], 2 * phi[None], 0 * phi[None])
+        s.step(60000 if case["D1"] == case["D2"] else 120000)
+        f = s.fields()
+        flat = f["c1"][0] + case["Keq"] * f["c2"][0]
+        tot = s.conserved()
+        level = case["Keq"] * tot[1] / (case["Keq"] * tot[0] + (N - tot[0]))
+        assert np.abs(flat - level).max() < 2e-3
+        if case["printed_level_of_c1_plus_Kc2"] is not None:
+            assert level == pytest.approx(case["printed_level_of_c1_plus_Kc2"], abs=0.01)
+        levels.append(level)
+    # cases 2 and 3 differ only in D1 and share the equilibrium
+    assert levels[1] == pytest.approx(levels[2], abs=1e-9)
+
+
+# ------------------------------------------------------------ heat kernel --
+def _gaussian_periodic(i, xc, var, N, amp, s0):
+    return sum(amp * sqrt(s0 / var) * np.exp(-(i - xc + m * N) ** 2 / (2 * var))
+               for m in range(-6, 7))
+
+
+def test_pseudo_single_phase_is_plain_diffusion():
+    g = json.load(open(os.path.join(GOLDEN, "pseudo_single_phase.json")))
+    N = g["domain"]["N"]
+    dx = (g["domain"]["x_max"] - g["domain"]["x_min"]) / N
+    xs = g["domain"]["x_min"] + dx * np.arange(N)
+    sdf = (-(xs - 0.5) * (xs + 0.5)) / dx
+    D = 0.1
+    s0 = 1.0 / 8.0 / dx ** 2          # variance of 5 exp(-4 x^2) in nodes^2
+    i = np.arange(N)
+    # 5 exp(-4 x^2) summed over its periodic images, so that the periodic
+    # heat kernel gives the exact solution at every later time
+    c0 = _gaussian_periodic(i, N / 2, s0, N, 5.0, s0)
+    for single_phase in (True, False):
+        phi = np.ones(N) if single_phase else tanh_phi(sdf, 4.0)
+        p = dict(wl.BASE, nx=N, ny=1, D1=D, D2=D, Keq=1.0, A=1000 * dx * dx)
+        s = oracle.OracleSim(p)
+        s.init_fields(phi[None], (c0 * phi)[None], (c0 * (1 - phi))[None])
+        steps = 2000
+        s.step(steps)
+        f = s.fields()
+        c = f["c1"][0] + f["c2"][0]
+        exact = _gaussian_periodic(i, N / 2, s0 + 2 * D * steps, N, 5.0, s0)
+        err = np.abs(c - exact).max() / exact.max()
+        assert err < (2e-3 if single_phase else 2e-2)
+
+
+# ------------------------------------------------------------- Poiseuille --
+@pytest.mark.parametrize("model,c1,beta", [(0, 0.0, 0.0), (1, 0.6, 0.0), (2, 0.5, 1.3)])
+def test_poiseuille_with_each_viscosity_relation(model, c1, beta):
+    H, Fx = 32, 1e-6
+    p = dict(wl.BASE, nx=1, ny=H, wall_y=1, mu1=0.1, mu2=0.02, Fx=Fx, A=0.0,
+             visc_model=model, visc_beta=beta)
+    s = oracle.OracleSim(p)
+    s.init_fields(np.ones((H, 1)), c1 * np.ones((H, 1)), np.zeros((H, 1)))
+    s.step(40000)
+    f = s.fields()
+    mu = [0.1, 0.1 ** c1, 0.1 * np.exp(-beta * c1)][model]
+    assert f["mu"][0, 0] == pytest.approx(mu, rel=1e-8)
+    y = np.arange(H) + 0.5          # half-way walls at y = -1/2 and y = H - 1/2
+    exact = Fx / (2 * mu) * y * (H - y)
+    assert np.abs(f["ux"][:, 0] - exact).max() / exact.max() < 0.01
+    assert np.abs(f["uy"]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- symmetry --
+def test_centred_droplet_keeps_mirror_and_transpose_symmetry():
+    n = 32
+    w = wl.droplet64(nx=n, ny=n, R=8.0, rho2=0.1, mu2=0.05, gx=0.0)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, 1.0, 0.2)
+    s.step(300)
+    f = s.fields()
+    # reflection x -> n - x about the centre x = n/2 (node n/2 maps to itself)
+    refl = lambda a: np.roll(a[:, ::-1], 1, axis=1)
+    assert np.abs(f["ux"]).max() > 1e-7
+    assert np.allclose(refl(f["phi"]), f["phi"], atol=1e-12)
+    assert np.allclose(refl(f["ux"]), -f["ux"], atol=1e-12)
+    assert np.allclose(f["ux"], f["uy"].T, atol=1e-12)
+    assert np.allclose(f["p"], f["p"].T, atol=1e-12)
+    assert np.allclose(f["c1"], f["c1"].T, atol=1e-12)
