@@ -1,0 +1,328 @@
+"""Benchmark of the fused phase-field LB step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload bubble1024x2048|droplets8192] [--precision fp32|fp64]
+
+One step = one pass of the whole hot path over the grid: pull-streaming of
+f, g, h1, h2, zeroth moments, stencils, flow macros, collision of the four
+lattices and the store (one launch of the fused kernel).  The default workload
+is the 1024 x 2048 wall-bounded rising bubble (density ratio 1000, viscosity
+ratio 100, mu = mu0 exp(-beta T)), FP32.  Its state (0.5 GB) is larger than
+L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Metric: MLUPS (million lattice-node updates per
+second), whole job.  Multi-GPU: one process per GPU (torchrun), each runs an
+independent replica of the workload (the path is data parallel per case; there
+is no exchange step), scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "fused_step_fp32_bubble1024x2048.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2402_15752_gb300", "csrc", f)
+                  for f in ("lbm_kernels.cuh", "lbm_internal.h")]
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bubble1024x2048", choices=["bubble1024x2048", "droplets8192"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_profile_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_FILE):
+        return None
+    rec = {}
+    for line in open(PROFILE_FILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(PEAKS_FILE))["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name, cells_cap=None):
+    from paper_2402_15752_gb300 import workloads as wl
+    if cells_cap is None:
+        return wl.get(name)
+    # bounded sample: the same workload with both sides scaled down
+    w = wl.get(name)
+    nx, ny = int(w.params["nx"]), int(w.params["ny"])
+    s = 1.0
+    while (nx * s) * (ny * s) > cells_cap and s > 1 / 64:
+        s /= 2
+    if s == 1.0:
+        return w
+    if name == "bubble1024x2048":
+        return wl.bubble1024x2048(nx=int(nx * s), ny=int(ny * s))
+    return wl.droplets8192(nx=int(nx * s), ny=int(ny * s))
+
+
+def oracle_mlups(name, steps_budget_s, cells_cap, min_steps=2):
+    """Time the FP64 CPU oracle (one thread) on a bounded sample of the workload."""
+    import oracle
+    w = make_workload(name, cells_cap)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+    t = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t
+    steps = max(min_steps, int(steps_budget_s / max(one, 1e-6)))
+    t = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t
+    return w.cells * steps / dt / 1e6, w, steps, dt
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    full = make_workload(args.workload)
+    # each step a bounded sample so that warmup + steps end within ~2-3 minutes
+    per_step_cells = int(max(4096, min(full.cells, 0.6e6 * 150.0 / max(1, args.steps + args.warmup))))
+    w = make_workload(args.workload, per_step_cells)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+    s.step(args.warmup)
+    t = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t
+    value = w.cells * args.steps / dt / 1e6
+    sample = "%s scaled to %dx%d (%d nodes), %d steps" % (args.workload, w.params["nx"],
+                                                         w.params["ny"], w.cells, args.steps)
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nx": full.params["nx"], "ny": full.params["ny"],
+                   "sample_nx": w.params["nx"], "sample_ny": w.params["ny"]},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2402_15752_gb300 import Simulation
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the GPU path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = make_workload(args.workload)
+    sim = Simulation(w.params, precision=args.precision, device=dev)
+    sim.init(w.sdf, w.c1_tilde, w.c2_tilde)
+    stream = sim.stream
+    sim.step(max(3, args.warmup))
+    sim.sync()
+
+    # ---- device-timed region: K fused steps, inputs resident in HBM ----
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    sampler = ClockSampler(int(phys) if phys.isdigit() else local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    sim.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    cells = w.cells
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- roofline of the fused kernel (the only kernel in the timed region) ----
+    q = int(w.params.get("scalar_q", 5))
+    elem = 8 if args.precision == "fp64" else 4
+    bytes_per_cell = 2 * (18 + 2 * q) * elem + 2 * 5 * elem
+    launch_s = ms * 1e-3 / args.steps
+    achieved = bytes_per_cell * cells / launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = read_profile_traffic() if (args.workload == "bubble1024x2048" and args.precision == "fp32") else None
+
+    # ---- end to end through the public API, host buffers, copies timed ----
+    e2e = None
+    if not args.no_e2e:
+        sdf_host = torch.from_numpy(np.ascontiguousarray(w.sdf, dtype=np.float64)).pin_memory()
+        out_host = torch.empty((6, w.params["ny"], w.params["nx"]), dtype=torch.float32).pin_memory()
+        names = ("phi", "ux", "uy", "p", "c1", "c2")
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.init(sdf_host, w.c1_tilde, w.c2_tilde)
+        sim.step(args.steps)
+        sim.fields(names=names, dtype="f32", out=out_host.numpy())
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ems = max_over_ranks(t0.elapsed_time(t1))
+        e2e = {"value": world * cells * args.steps / (ems * 1e-3) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": cells * 8 / args.steps,
+               "d2h_bytes_per_step": 6 * cells * 4 / args.steps}
+        sim.sync()
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, sw, steps, dt = oracle_mlups(args.workload, 15.0, 256 * 512)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "%s scaled to %dx%d, %d steps, %.1f s, FP64, one thread" % (
+                   args.workload, sw.params["nx"], sw.params["ny"], steps, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nx": w.params["nx"], "ny": w.params["ny"],
+                       "bc": "walls" if w.params["wall_x"] else "periodic", "scalar_q": q,
+                       "precision": args.precision, "l2": "state larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "bytes_per_cell": bytes_per_cell},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

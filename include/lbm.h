@@ -1,0 +1,164 @@
+/*
+ * liblbm -- GB300-native phase-field lattice Boltzmann solver for two-phase
+ * flow with interfacial mass/heat transfer (Chen, Zhan, Chai & Shi,
+ * arXiv 2402.15752).  C ABI: plain pointers and sizes, no C++ or torch types.
+ *
+ * One time step (lbm_step) is the paper's coupled collide-and-stream over four
+ * lattices, in lattice units (dx = dt = 1, cs^2 = 1/3):
+ *   f  (D2Q9)  conservative Allen-Cahn phase field          Sec. III A, Eqs. (23)-(27)
+ *   g  (D2Q9)  pressure-based incompressible two-phase flow Sec. III B, Eqs. (28)-(33)
+ *              with the surface-tension force mu_phi grad(phi), Eqs. (4)-(5)
+ *   h1, h2     two-scalar mass/heat transfer with the auxiliary interfacial
+ *   (D2Q5|Q9)  source H~, Sec. III C, Eqs. (34)-(38)
+ * gradients and the Laplacian use the isotropic central stencils of
+ * Eqs. (41)-(42); viscosity is linear in phi (Eq. 7), follows Eq. (48), or
+ * mu = mu_lin(phi) * exp(-visc_beta * (c1 + c2)).
+ *
+ * Ownership.  The caller owns the device workspace, the CUDA stream and every
+ * input/output buffer.  The library allocates no device memory; it owns only
+ * the small host-side handle (plus 16 bytes of pinned host memory for the
+ * asynchronous status word).  Every call is asynchronous on the handle's
+ * stream unless its comment says it synchronises.
+ *
+ * Errors.  Every int-returning call returns LBM_OK (0) or a negative LBM_ERR_*
+ * code; lbm_last_error() gives a message.  No C++ exception crosses the ABI
+ * and no kernel traps or asserts.
+ *
+ * Field layout.  Every host or device field is row-major, index = y*nx + x,
+ * node coordinates x = 0..nx-1, y = 0..ny-1.
+ */
+#ifndef PFLBM_LBM_H
+#define PFLBM_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LBM_OK                0
+#define LBM_ERR_ARG          (-1) /* bad pointer, size, enum or physical parameter   */
+#define LBM_ERR_UNSTABLE_TAU (-2) /* a relaxation time would be <= 1/2                */
+#define LBM_ERR_WORKSPACE    (-3) /* workspace too small or misaligned                */
+#define LBM_ERR_CUDA         (-4) /* a CUDA runtime call failed                       */
+#define LBM_ERR_NONFINITE    (-5) /* a NaN/Inf macro value was produced by a step     */
+#define LBM_ERR_TIMEOUT      (-6) /* a bounded device wait gave up (batched runner)   */
+
+/* ---- enums ---- */
+#define LBM_BC_PERIODIC 0
+#define LBM_BC_WALL     1 /* half-way bounce-back (Sec. IV): no-slip, no-flux */
+
+#define LBM_FP64           0 /* FP64 storage and arithmetic                      */
+#define LBM_FP32           1 /* FP32 storage and arithmetic                      */
+
+#define LBM_VISC_LINEAR 0 /* mu = phi (mu1 - mu2) + mu2                 Eq. (7)  */
+#define LBM_VISC_LOG_C  1 /* log mu = c1 log mu1 + c2 log mu2          Eq. (48) */
+#define LBM_VISC_EXP_T  2 /* mu = [phi (mu1 - mu2) + mu2] exp(-visc_beta (c1 + c2)) */
+
+/* field mask bits for lbm_get_fields; fields are written in this order */
+#define LBM_FIELD_PHI (1u << 0)
+#define LBM_FIELD_UX  (1u << 1)
+#define LBM_FIELD_UY  (1u << 2)
+#define LBM_FIELD_P   (1u << 3)
+#define LBM_FIELD_C1  (1u << 4)
+#define LBM_FIELD_C2  (1u << 5)
+#define LBM_FIELD_RHO (1u << 6)
+#define LBM_FIELD_MU  (1u << 7)
+#define LBM_FIELD_ALL 0xffu
+
+#define LBM_OUT_F64 0
+#define LBM_OUT_F32 1
+
+/*
+ * Problem parameters, in lattice units, as the paper states the problem:
+ * Eqs. (4)-(7) and (17)-(18) for the physics, Eqs. (27), (33), (38) for the
+ * relaxation times derived from M, mu/rho and D_k.  Phase 1 is phi = 1.
+ */
+typedef struct {
+    int32_t nx, ny;        /* grid nodes, each >= 1                                  */
+    int32_t bc_x, bc_y;    /* LBM_BC_PERIODIC or LBM_BC_WALL                         */
+    int32_t scalar_q;      /* 5 (D2Q5) or 9 (D2Q9) for h1, h2                        */
+    int32_t precision;     /* LBM_FP64 or LBM_FP32                                   */
+    double W, M, sigma;    /* interface width, mobility, surface tension (> 0, > 0, >= 0) */
+    double rho1, rho2;     /* densities (> 0)                                        */
+    double mu1, mu2;       /* dynamic viscosities (> 0)                              */
+    double D1, D2;         /* scalar diffusivities (> 0)                             */
+    double Keq, A;         /* equilibrium jump K_eq (> 0), inverse time scale A (>= 0) */
+    double gx, gy;         /* body force G = (rho - g_rho_ref) (gx, gy) + (Fx, Fy)   */
+    double g_rho_ref;
+    double Fx, Fy;
+    int32_t visc_model;    /* LBM_VISC_*                                             */
+    double visc_beta;      /* exponent of LBM_VISC_EXP_T                             */
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of device workspace the parameters need (0 if the parameters are invalid).
+ * Layout per node: two population buffers (28 values for scalar_q = 5, 36 for 9),
+ * five previous-step macros, plus a few KB of reduction partials and flags. */
+size_t lbm_workspace_bytes(const lbm_params* params);
+
+/* Validate parameters (Sec. III relaxation-time relations: every tau > 1/2),
+ * carve the caller's device workspace (256-byte aligned, >= lbm_workspace_bytes)
+ * and bind the CUDA stream (a cudaStream_t; NULL = legacy default stream).
+ * Host only: no kernel runs.  On success *out is a new handle. */
+int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_bytes,
+               void* cuda_stream, lbm_handle** out);
+
+/* Initial state from a signed-distance field l(x) (nx*ny doubles, host or device):
+ * phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1_tilde * phi, c2 = c2_tilde * (1 - phi),
+ * u = 0, p = 0.  Populations start at their equilibria (f_i = w_i phi, g_i = 0) and
+ * h_k,i = w_i (c_k -/+ S/2) so that Eq. (37) returns the given c_k; the time counter
+ * restarts at 0.  A host sdf is copied synchronously before the call returns. */
+int lbm_init(lbm_handle* h, const double* sdf, int32_t sdf_on_device,
+             double c1_tilde, double c2_tilde);
+
+/* Same, from explicit phi, c1, c2 fields (nx*ny doubles each, host or device). */
+int lbm_init_fields(lbm_handle* h, const double* phi, const double* c1, const double* c2,
+                    int32_t on_device);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  Returns LBM_ERR_NONFINITE if an
+ * earlier call's steps, already finished on the GPU, produced a NaN/Inf. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Macroscopic fields of the current state (the zeroth/first moments of the current
+ * populations, Eqs. (26), (32), (37), with the stencils of Eqs. (41)-(42)).
+ * out receives popcount(mask) consecutive fields of nx*ny values, in mask-bit order,
+ * as doubles (LBM_OUT_F64) or floats (LBM_OUT_F32).  out_on_device = 0: out is host
+ * memory and the call synchronises the stream before returning. */
+int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_device,
+                   int32_t out_dtype);
+
+/* {sum phi, sum (c1 + c2)} over all nodes of the current state, reduced on the GPU in
+ * FP64 in a fixed order (deterministic).  Synchronises; also reports a pending
+ * non-finite flag as LBM_ERR_NONFINITE. */
+int lbm_conserved(lbm_handle* h, double out[2]);
+
+/* Synchronise the stream and report LBM_ERR_NONFINITE if any finished step
+ * produced a NaN/Inf; clears nothing. */
+int lbm_sync(lbm_handle* h);
+
+/* Checkpoint: the populations and previous-step macros of the current state.
+ * lbm_state_bytes gives the size; get/set copy to/from caller memory (host or
+ * device) and synchronise.  Restoring then stepping is bit-identical to never
+ * having stopped. */
+size_t lbm_state_bytes(const lbm_handle* h);
+int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device);
+int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_device);
+
+/* Steps taken since the last init or set_state. */
+int64_t lbm_time(const lbm_handle* h);
+
+/* Release the handle (and its CUDA graphs/events); the workspace stays the caller's. */
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last error on this handle; with h == NULL, the calling thread's
+ * last lbm_create/lbm_workspace_bytes error. */
+const char* lbm_last_error(const lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

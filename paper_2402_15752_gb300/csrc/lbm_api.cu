@@ -1,0 +1,479 @@
+// C ABI of liblbm (declared in include/lbm.h): parameter validation, workspace
+// carving, stepping with CUDA graphs, field read-back, conserved sums,
+// checkpoints and error reporting.  Host code plus the small init kernel that
+// turns a signed-distance field into phi, c1, c2.
+#include "lbm.h"
+#include "lbm_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+namespace {
+
+constexpr double CS2 = 1.0 / 3.0;
+constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity is kept)
+constexpr size_t ALIGN = 256;
+
+thread_local char g_thread_error[512] = "";
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int nq;             // populations per node
+    size_t elem, relem; // bytes of a stored population / of a previous-step macro
+    int nxb;            // 32-node blocks per row
+    size_t pop_elems, prev_elems;
+    size_t pop_bytes, prev_bytes, part_bytes, misc_bytes;
+    size_t off_pop[2], off_prev, off_part, off_misc, total;
+};
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Returns LBM_OK or an error code with a message in `err`.
+int validate(const lbm_params* p, char* err, size_t n) {
+    if (!p) { snprintf(err, n, "params is NULL"); return LBM_ERR_ARG; }
+    if (p->nx < 1 || p->ny < 1) { snprintf(err, n, "nx and ny must be >= 1 (got %d x %d)", p->nx, p->ny); return LBM_ERR_ARG; }
+    if (p->nx > (1 << 28) || p->ny > (1 << 28) || (double)p->nx * p->ny > 4e9) { snprintf(err, n, "grid %d x %d too large", p->nx, p->ny); return LBM_ERR_ARG; }
+    if ((p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_WALL) || (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALL)) {
+        snprintf(err, n, "bc_x/bc_y must be LBM_BC_PERIODIC or LBM_BC_WALL"); return LBM_ERR_ARG;
+    }
+    if (p->scalar_q != 5 && p->scalar_q != 9) { snprintf(err, n, "scalar_q must be 5 or 9 (got %d)", p->scalar_q); return LBM_ERR_ARG; }
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) { snprintf(err, n, "unknown precision %d", p->precision); return LBM_ERR_ARG; }
+    if (p->visc_model < LBM_VISC_LINEAR || p->visc_model > LBM_VISC_EXP_T) { snprintf(err, n, "unknown visc_model %d", p->visc_model); return LBM_ERR_ARG; }
+    if (!finite_pos(p->W)) { snprintf(err, n, "W must be > 0"); return LBM_ERR_ARG; }
+    if (!finite_pos(p->rho1) || !finite_pos(p->rho2)) { snprintf(err, n, "rho1, rho2 must be > 0"); return LBM_ERR_ARG; }
+    if (!finite_pos(p->Keq)) { snprintf(err, n, "Keq must be > 0"); return LBM_ERR_ARG; }
+    if (!std::isfinite(p->sigma) || p->sigma < 0 || !std::isfinite(p->A) || p->A < 0) { snprintf(err, n, "sigma and A must be finite and >= 0"); return LBM_ERR_ARG; }
+    const double fin[] = {p->gx, p->gy, p->g_rho_ref, p->Fx, p->Fy, p->visc_beta, p->M, p->D1, p->D2, p->mu1, p->mu2};
+    for (double v : fin) if (!std::isfinite(v)) { snprintf(err, n, "parameters must be finite"); return LBM_ERR_ARG; }
+    // Eqs. (27), (33), (38): every relaxation time must exceed 1/2
+    if (!(p->M > 0)) { snprintf(err, n, "tau_f = M/cs^2 + 1/2 <= 1/2 (M = %g)", p->M); return LBM_ERR_UNSTABLE_TAU; }
+    if (!(p->D1 > 0) || !(p->D2 > 0)) { snprintf(err, n, "tau_h = D/cs^2 + 1/2 <= 1/2 (D1 = %g, D2 = %g)", p->D1, p->D2); return LBM_ERR_UNSTABLE_TAU; }
+    if (!(p->mu1 > 0) || !(p->mu2 > 0)) { snprintf(err, n, "tau_g = mu/(rho cs^2) + 1/2 <= 1/2 (mu1 = %g, mu2 = %g)", p->mu1, p->mu2); return LBM_ERR_UNSTABLE_TAU; }
+    return LBM_OK;
+}
+
+Layout layout_of(const lbm_params* p) {
+    Layout L;
+    L.nq = 18 + 2 * p->scalar_q;  // f, g, h1, h2
+    L.elem = p->precision == LBM_FP64 ? 8 : 4;
+    L.relem = p->precision == LBM_FP64 ? 8 : 4;
+    L.nxb = (p->nx + 31) / 32;
+    L.pop_elems = (size_t)p->ny * L.nxb * L.nq * 32;
+    L.prev_elems = (size_t)p->ny * L.nxb * 5 * 32;
+    L.pop_bytes = align_up(L.pop_elems * L.elem, ALIGN);
+    L.prev_bytes = align_up(L.prev_elems * L.relem, ALIGN);
+    L.part_bytes = align_up((size_t)lbm::RED_BLOCKS * 2 * sizeof(double), ALIGN);
+    L.misc_bytes = ALIGN;
+    L.off_pop[0] = 0;
+    L.off_pop[1] = L.pop_bytes;
+    L.off_prev = 2 * L.pop_bytes;
+    L.off_part = L.off_prev + L.prev_bytes;
+    L.off_misc = L.off_part + L.part_bytes;
+    L.total = L.off_misc + L.misc_bytes;
+    return L;
+}
+
+template <typename R>
+lbm::Coeffs<R> coeffs_of(const lbm_params* p) {
+    lbm::Coeffs<R> C;
+    const double tf = p->M / CS2 + 0.5, t1 = p->D1 / CS2 + 0.5, t2 = p->D2 / CS2 + 0.5;
+    C.omega_f = R(1.0 / tf);  C.force_f = R(1.0 - 0.5 / tf);
+    C.omega_h1 = R(1.0 / t1); C.force_h1 = R(1.0 - 0.5 / t1);
+    C.omega_h2 = R(1.0 / t2); C.force_h2 = R(1.0 - 0.5 / t2);
+    C.beta4 = R(4.0 * 12.0 * p->sigma / p->W);
+    C.kappa = R(1.5 * p->sigma * p->W);
+    C.rho1 = R(p->rho1); C.rho2 = R(p->rho2); C.drho = R(p->rho1 - p->rho2);
+    C.mu2 = R(p->mu2); C.dmu = R(p->mu1 - p->mu2);
+    C.log_mu1 = R(std::log(p->mu1)); C.log_mu2 = R(std::log(p->mu2));
+    C.visc_beta = R(p->visc_beta);
+    C.D1D2 = R(p->D1 * p->D2); C.KD1 = R(p->Keq * p->D1); C.D2 = R(p->D2); C.K = R(p->Keq);
+    C.halfA = R(0.5 * p->A); C.A = R(p->A);
+    C.four_over_W = R(4.0 / p->W);
+    C.gx = R(p->gx); C.gy = R(p->gy); C.g_rho_ref = R(p->g_rho_ref);
+    C.Fx = R(p->Fx); C.Fy = R(p->Fy);
+    C.visc_model = p->visc_model;
+    return C;
+}
+
+__global__ void sdf_to_fields_kernel(const double* __restrict__ sdf, double* phi, double* c1, double* c2,
+                                     size_t n, double W, double c1t, double c2t) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double l = sdf[k];
+        const double ph = 0.5 + 0.5 * tanh(2.0 * l / W);  // Eq. (2)
+        phi[k] = ph;
+        c1[k] = c1t * ph;
+        c2[k] = c2t * (1.0 - ph);
+    }
+}
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int dev) : want(dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard() { if (prev >= 0 && prev != want) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+namespace lbm {
+cudaError_t launch_sdf_to_fields(const double* sdf, double* phi, double* c1, double* c2, size_t n,
+                                 double W, double c1t, double c2t, cudaStream_t s) {
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    sdf_to_fields_kernel<<<blocks, 256, 0, s>>>(sdf, phi, c1, c2, n, W, c1t, c2t);
+    return cudaGetLastError();
+}
+}  // namespace lbm
+
+struct lbm_handle {
+    lbm_params p;
+    Layout L;
+    lbm::Geometry geo;
+    lbm::Coeffs<float> cf;
+    lbm::Coeffs<double> cd;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    uint8_t* ws = nullptr;
+    int cur = 0;
+    int64_t t = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned* h_status = nullptr;
+    cudaEvent_t status_ev = nullptr;
+    bool status_pending = false;
+    bool nonfinite = false;  // sticky until the next init / set_state
+    char err[512] = "";
+
+    void* pop(int k) const { return ws + L.off_pop[k]; }
+    void* prev() const { return ws + L.off_prev; }
+    double* partials() const { return reinterpret_cast<double*>(ws + L.off_part); }
+    unsigned* flag() const { return reinterpret_cast<unsigned*>(ws + L.off_misc); }
+    double* sums() const { return reinterpret_cast<double*>(ws + L.off_misc + 16); }
+    bool f64() const { return p.precision == LBM_FP64; }
+
+    int fail(int code, const char* what, cudaError_t e = cudaSuccess) {
+        if (e != cudaSuccess) snprintf(err, sizeof(err), "%s: %s", what, cudaGetErrorString(e));
+        else snprintf(err, sizeof(err), "%s", what);
+        return code;
+    }
+
+    cudaError_t step_once(int from, cudaStream_t s) {
+        if (f64())
+            return lbm::launch_step<double, double>(pop(from), pop(from ^ 1), prev(), geo, cd, p.scalar_q, flag(), s);
+        return lbm::launch_step<float, float>(pop(from), pop(from ^ 1), prev(), geo, cf, p.scalar_q, flag(), s);
+    }
+
+    cudaError_t fields(int from, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+        if (f64())
+            return lbm::launch_fields<double, double>(pop(from), geo, cd, p.scalar_q, mask, out, out_f64, s);
+        return lbm::launch_fields<float, float>(pop(from), geo, cf, p.scalar_q, mask, out, out_f64, s);
+    }
+
+    cudaError_t build_graph(int parity) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        int c = parity;
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < GRAPH_STEPS && le == cudaSuccess; ++k, c ^= 1) le = step_once(c, capture);
+        e = cudaStreamEndCapture(capture, &g);
+        if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&graph[parity], g, 0);
+        cudaGraphDestroy(g);
+        return e;
+    }
+
+    // Non-blocking look at the status word copied back after the last lbm_step.
+    bool nonfinite_seen() {
+        if (status_pending && cudaEventQuery(status_ev) == cudaSuccess) {
+            status_pending = false;
+            if (*h_status != 0u) nonfinite = true;
+        }
+        return nonfinite;
+    }
+};
+
+// Rows per CTA of the step kernel: the strip height that fills the SMs in whole
+// waves with the least idle capacity, counting the two halo rows each strip
+// evaluates twice.
+static int choose_strip_height(const lbm_handle* h) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 1;
+    int per_sm = h->f64() ? lbm::step_blocks_per_sm<double, double>(h->p.scalar_q)
+                          : lbm::step_blocks_per_sm<float, float>(h->p.scalar_q);
+    cudaGetLastError();
+    if (per_sm <= 0) per_sm = 1;
+    const long long slots = (long long)sms * per_sm;
+    const int ny = h->p.ny;
+    const long long cx = (h->p.nx + lbm::STRIP_W - 1) / lbm::STRIP_W;
+    int best_h = ny;
+    double best = -1.0;
+    for (int waves = 1; waves <= 16; ++waves) {
+        long long cy = std::max<long long>(1, waves * slots / cx);
+        int H = (int)std::max<long long>(1, (ny + cy - 1) / cy);
+        if (H < 4 && ny >= 4) H = 4;
+        H = std::max(H, (ny + 65534) / 65535);  // grid.y <= 65535
+        const long long ctas = cx * ((ny + H - 1) / H);
+        const long long used_waves = (ctas + slots - 1) / slots;
+        const double fill = (double)ctas / (double)(used_waves * slots);
+        const double eff = fill * (double)H / (double)(H + 2) * (double)ny / (double)(((ny + H - 1) / H) * H);
+        if (eff > best + 1e-9) { best = eff; best_h = H; }
+    }
+    return best_h;
+}
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_params* params) {
+    if (validate(params, g_thread_error, sizeof(g_thread_error)) != LBM_OK) return 0;
+    return layout_of(params).total;
+}
+
+int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+               lbm_handle** out) {
+    if (!out) { snprintf(g_thread_error, sizeof(g_thread_error), "out is NULL"); return LBM_ERR_ARG; }
+    *out = nullptr;
+    int rc = validate(params, g_thread_error, sizeof(g_thread_error));
+    if (rc != LBM_OK) return rc;
+    const Layout L = layout_of(params);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % ALIGN) != 0) {
+        snprintf(g_thread_error, sizeof(g_thread_error), "workspace must be a non-NULL %zu-byte aligned device pointer", ALIGN);
+        return LBM_ERR_WORKSPACE;
+    }
+    if (workspace_bytes < L.total) {
+        snprintf(g_thread_error, sizeof(g_thread_error), "workspace too small: %zu bytes given, %zu needed", workspace_bytes, L.total);
+        return LBM_ERR_WORKSPACE;
+    }
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        snprintf(g_thread_error, sizeof(g_thread_error), "workspace is not device memory");
+        return LBM_ERR_WORKSPACE;
+    }
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) { snprintf(g_thread_error, sizeof(g_thread_error), "out of host memory"); return LBM_ERR_ARG; }
+    h->p = *params;
+    h->L = L;
+    h->geo.nx = params->nx; h->geo.ny = params->ny; h->geo.nxb = L.nxb;
+    h->geo.wall_x = params->bc_x == LBM_BC_WALL; h->geo.wall_y = params->bc_y == LBM_BC_WALL;
+    h->geo.strip_h = params->ny;
+    h->cf = coeffs_of<float>(params);
+    h->cd = coeffs_of<double>(params);
+    h->device = attr.device;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ws = static_cast<uint8_t*>(d_workspace);
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_status), 16);
+    if (e != cudaSuccess) {
+        snprintf(g_thread_error, sizeof(g_thread_error), "CUDA setup failed: %s", cudaGetErrorString(e));
+        lbm_destroy(h);
+        return LBM_ERR_CUDA;
+    }
+    *h->h_status = 0u;
+    h->geo.strip_h = choose_strip_height(h);
+    *out = h;
+    return LBM_OK;
+}
+
+static int init_common(lbm_handle* h, const double* phi, const double* c1, const double* c2) {
+    cudaError_t e;
+    if (h->f64())
+        e = lbm::launch_init<double, double>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd, h->p.scalar_q, h->stream);
+    else
+        e = lbm::launch_init<float, float>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd, h->p.scalar_q, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "init kernel", e);
+    h->cur = 0;
+    h->t = 0;
+    h->status_pending = false;
+    h->nonfinite = false;
+    *h->h_status = 0u;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle* h, const double* sdf, int32_t sdf_on_device, double c1_tilde, double c2_tilde) {
+    if (!h) return LBM_ERR_ARG;
+    if (!sdf) return h->fail(LBM_ERR_ARG, "sdf is NULL");
+    if (!std::isfinite(c1_tilde) || !std::isfinite(c2_tilde)) return h->fail(LBM_ERR_ARG, "c1_tilde/c2_tilde must be finite");
+    DeviceGuard dg(h->device);
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    double* st = static_cast<double*>(h->pop(1));  // staging: the population buffer the first step writes
+    double *phi = st, *c1 = st + n, *c2 = st + 2 * n;
+    cudaError_t e = cudaSuccess;
+    const double* src = sdf;
+    if (!sdf_on_device) {
+        e = cudaMemcpyAsync(phi, sdf, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        src = phi;
+    }
+    if (e == cudaSuccess) e = lbm::launch_sdf_to_fields(src, phi, c1, c2, n, h->p.W, c1_tilde, c2_tilde, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_init", e);
+    return init_common(h, phi, c1, c2);
+}
+
+int lbm_init_fields(lbm_handle* h, const double* phi, const double* c1, const double* c2, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (!phi || !c1 || !c2) return h->fail(LBM_ERR_ARG, "phi, c1, c2 must be non-NULL");
+    DeviceGuard dg(h->device);
+    if (on_device) return init_common(h, phi, c1, c2);
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    double* st = static_cast<double*>(h->pop(1));
+    cudaError_t e = cudaMemcpyAsync(st, phi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + n, c1, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + 2 * n, c2, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_init_fields copy", e);
+    return init_common(h, st, st + n, st + 2 * n);
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    if (!h) return LBM_ERR_ARG;
+    if (nsteps < 0) return h->fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (h->nonfinite_seen()) return h->fail(LBM_ERR_NONFINITE, "a previous step produced a non-finite macro value");
+    if (nsteps == 0) return LBM_OK;
+    DeviceGuard dg(h->device);
+    int64_t left = nsteps;
+    cudaError_t e = cudaSuccess;
+    if (left >= GRAPH_STEPS) {
+        if (!h->graph[h->cur]) e = h->build_graph(h->cur);
+        while (e == cudaSuccess && left >= GRAPH_STEPS) {
+            e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+            left -= GRAPH_STEPS;  // even count: the state stays in buffer cur
+        }
+    }
+    while (e == cudaSuccess && left > 0) {
+        e = h->step_once(h->cur, h->stream);
+        h->cur ^= 1;
+        --left;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_status, h->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->status_ev, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_step", e);
+    h->status_pending = true;
+    h->t += nsteps - left;
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_device, int32_t out_dtype) {
+    if (!h) return LBM_ERR_ARG;
+    mask &= LBM_FIELD_ALL;
+    if (!mask || !out) return h->fail(LBM_ERR_ARG, "empty field mask or NULL output");
+    if (out_dtype != LBM_OUT_F64 && out_dtype != LBM_OUT_F32) return h->fail(LBM_ERR_ARG, "out_dtype must be LBM_OUT_F64 or LBM_OUT_F32");
+    DeviceGuard dg(h->device);
+    const int f64 = out_dtype == LBM_OUT_F64;
+    cudaError_t e = cudaSuccess;
+    if (out_on_device) {
+        e = h->fields(h->cur, mask, out, f64, h->stream);
+        if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_fields", e);
+        return LBM_OK;
+    }
+    // host output: evaluate into the idle population buffer, in batches that fit
+    const size_t per_field = (size_t)h->p.nx * h->p.ny * (f64 ? 8 : 4);
+    const size_t batch = h->L.pop_bytes / per_field;
+    uint8_t* dst = static_cast<uint8_t*>(out);
+    void* staging = h->pop(h->cur ^ 1);
+    uint32_t rest = mask;
+    while (rest && e == cudaSuccess) {
+        uint32_t sub = 0;
+        size_t k = 0;
+        for (int b = 0; b < 8 && k < batch; ++b)
+            if (rest & (1u << b)) { sub |= 1u << b; ++k; }
+        rest &= ~sub;
+        e = h->fields(h->cur, sub, staging, f64, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, staging, k * per_field, cudaMemcpyDeviceToHost, h->stream);
+        dst += k * per_field;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_fields", e);
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaMemcpyAsync(h->h_status, h->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_sync", e);
+    h->status_pending = false;
+    if (*h->h_status) h->nonfinite = true;
+    if (h->nonfinite) return h->fail(LBM_ERR_NONFINITE, "a step produced a non-finite macro value");
+    return LBM_OK;
+}
+
+int lbm_conserved(lbm_handle* h, double out[2]) {
+    if (!h) return LBM_ERR_ARG;
+    if (!out) return h->fail(LBM_ERR_ARG, "out is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = h->f64()
+        ? lbm::launch_conserved<double>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(), h->stream)
+        : lbm::launch_conserved<float>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(), h->stream);
+    double tmp[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->sums(), 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_conserved", e);
+    const int rc = lbm_sync(h);
+    out[0] = tmp[0];
+    out[1] = tmp[1];
+    return rc;
+}
+
+size_t lbm_state_bytes(const lbm_handle* h) {
+    if (!h) return 0;
+    return h->L.pop_elems * h->L.elem + h->L.prev_elems * h->L.relem;
+}
+
+int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
+    if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
+    DeviceGuard dg(h->device);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(buf, h->pop(h->cur), a, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<uint8_t*>(buf) + a, h->prev(), b, k, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_state", e);
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
+    if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
+    DeviceGuard dg(h->device);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(h->pop(0), buf, a, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->prev(), static_cast<const uint8_t*>(buf) + a, b, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_set_state", e);
+    h->cur = 0;
+    h->t = 0;
+    h->status_pending = false;
+    h->nonfinite = false;
+    *h->h_status = 0u;
+    return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    {
+        DeviceGuard dg(h->device);
+        if (h->stream || h->capture) cudaStreamSynchronize(h->stream);
+        for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
+        if (h->status_ev) cudaEventDestroy(h->status_ev);
+        if (h->capture) cudaStreamDestroy(h->capture);
+        if (h->h_status) cudaFreeHost(h->h_status);
+    }
+    delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err : g_thread_error; }
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Internal host/device interface of liblbm: storage layout, run constants and
+// the kernel launchers that the C ABI (lbm_api.cu) dispatches to.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Step kernel: a CTA of STRIP_WARPS warps owns STRIP_W consecutive columns and
+// marches up a strip of `strip_h` rows, one thread per column.
+constexpr int STRIP_WARPS = 4;
+constexpr int STRIP_W = 32 * STRIP_WARPS;
+constexpr int STRIP_MIN_BLOCKS = 5;  // occupancy target: caps registers at 102/thread
+// Blocks of the conserved-sum reduction (fixed, so the summation order is fixed).
+constexpr int RED_BLOCKS = 304;
+constexpr int RED_THREADS = 256;
+
+// Storage layout (array of structures of arrays, 32-node blocks).  Rows are cut
+// into blocks of 32 consecutive nodes; a block stores its NQ populations as NQ
+// runs of 32 values.  Value q of node (x, y) lives at element
+//     ((y * nxb + x / 32) * NQ + q) * 32 + x % 32,      nxb = ceil(nx / 32).
+// The population planes are f_0..f_8 -> q = 0..8, g_0..g_8 -> 9..17,
+// h1_0..h1_{Q-1} -> 18..17+Q, h2_0..h2_{Q-1} -> 18+Q..17+2Q.  A warp touches
+// 128 contiguous bytes per population (FP32), and every population of a node
+// sits at a compile-time offset from the node's first value.  The five
+// previous-step macros (phi, ux, uy, c1, c2) use the same layout with NQ = 5.
+struct Geometry {
+    int nx, ny, nxb;
+    int wall_x, wall_y;
+    int strip_h;  // rows per CTA of the step kernel
+};
+
+// Per-run constants, derived once on the host in double and cast to the
+// compute type R (float or double).
+template <typename R>
+struct Coeffs {
+    R omega_f, force_f;      // 1/tau_f, 1 - 1/(2 tau_f)
+    R omega_h1, force_h1;    // 1/tau_h1, 1 - 1/(2 tau_h1)
+    R omega_h2, force_h2;
+    R beta4, kappa;          // 4 beta = 48 sigma / W,  k = 3 sigma W / 2
+    R rho1, rho2, drho;      // drho = rho1 - rho2
+    R mu2, dmu;              // linear viscosity mu2 + dmu * phi
+    R log_mu1, log_mu2, visc_beta;
+    R D1D2, KD1, D2, K;      // D_m = D1 D2 / (K D1 (1 - phi) + D2 phi)
+    R halfA, A;
+    R four_over_W;
+    R gx, gy, g_rho_ref, Fx, Fy;
+    int visc_model;
+};
+
+inline size_t lattice_elems(const Geometry& g, int nq) { return (size_t)g.ny * g.nxb * nq * 32; }
+
+// Launchers (one instantiation per precision, defined in lbm_step_f32.cu /
+// lbm_step_f64.cu).  `src` holds the post-collision populations of the last
+// step (pull scheme: streaming happens on the read), `dst` receives the new
+// ones; `prev` holds phi, ux, uy, c1, c2 of the last step (updated in place).
+template <typename T, typename R>
+cudaError_t launch_step(const void* src, void* dst, void* prev, const Geometry& geo,
+                        const Coeffs<R>& C, int scalar_q, unsigned* flag, cudaStream_t s);
+
+// Macroscopic fields of the state in `src` (no collision), written as dense
+// nx*ny arrays in mask-bit order (double or float).
+template <typename T, typename R>
+cudaError_t launch_fields(const void* src, const Geometry& geo, const Coeffs<R>& C, int scalar_q,
+                          uint32_t mask, void* out, int out_f64, cudaStream_t s);
+
+// Initial populations from phi, c1, c2 (three dense nx*ny double arrays),
+// written pre-streamed so the first pulled read returns them.
+template <typename T, typename R>
+cudaError_t launch_init(const double* phi, const double* c1, const double* c2, void* pop,
+                        void* prev, const Geometry& geo, const Coeffs<double>& C, int scalar_q,
+                        cudaStream_t s);
+
+// phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1t phi, c2 = c2t (1 - phi), into
+// three dense staging arrays (sdf may alias phi).
+cudaError_t launch_sdf_to_fields(const double* sdf, double* phi, double* c1, double* c2, size_t n,
+                                 double W, double c1t, double c2t, cudaStream_t s);
+
+// {sum phi, sum(c1 + c2)} of the current state: block partials + a fixed-order final pass.
+template <typename T>
+cudaError_t launch_conserved(const void* pop, const Geometry& geo, int scalar_q,
+                             double* partials, double* out, cudaStream_t s);
+
+// CTAs of the step kernel that fit on one SM (for the strip-height choice).
+template <typename T, typename R>
+int step_blocks_per_sm(int scalar_q);
+
+}  // namespace lbm

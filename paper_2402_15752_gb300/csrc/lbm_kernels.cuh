@@ -1,0 +1,777 @@
+// Device code of the fused phase-field / flow / two-scalar LB step.
+//
+// Step kernel ("strip" design).  A CTA of 4 warps owns 128 consecutive columns
+// and marches up a strip of rows, one thread per column.  For row y it
+//   a. pulls g and reads the previous-step macros of its node (row y), and
+//      pulls f, h1, h2 of row y+1: streaming happens on the read (pull scheme),
+//      half-way bounce-back where the upstream node is behind a wall;
+//   b. forms the zeroth moments of row y+1: phi = sum f (Eq. 26) and the
+//      implicit c1, c2 of Eq. (37), solved exactly as a 2x2 system, into a
+//      4-row ring in shared memory (lanes 0 and 127 also cover the two halo
+//      columns);
+//   c. after one barrier, evaluates the D2Q9 isotropic stencils of Eqs. (41)-(42)
+//      for grad phi, lap phi, grad c1, grad c2 at row y from rows y-1..y+1;
+//   d. forms mu_phi (Eqs. 4-5), the force, u and p (Eq. 32), the viscosity and
+//      tau_g (Eq. 33 with Eq. 7, Eq. 48 or the exponential law) and the
+//      backward differences d/dt(chi u);
+//   e. collides f (Eqs. 23-25), g (Eqs. 28-31), h1 and h2 (Eqs. 34-36) in
+//      registers, with f, h1, h2 of row y kept from the previous iteration,
+//      and stores the post-collision populations at the node itself.
+// Each node's f, h1, h2 are read from DRAM once per step; only the two halo
+// rows and columns of a strip are pulled twice (L2 hits).
+//
+// The collisions are written in factored form, w_i [a + c_i . b + ...], and
+// the rest populations of f, h1, h2 take the exact post-collision sums minus
+// the moving populations, so rounding of the lattice weights cannot bias the
+// conserved totals.  Laplacians are formed from differences to the centre
+// node.
+//
+// Readings of points the paper leaves open (shared with the CPU oracle only
+// through their written statement): d/dt(chi u) = (chi u)^n - (chi u)^{n-1};
+// n = grad phi / (|grad phi| + 1e-4); mirror ghosts at walls for the stencils;
+// rho and mu use phi clipped to [0, 1]; D_m = 0 where its denominator <= 0.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---- lattice: D2Q9 order rest, +x, +y, -x, -y, (+,+), (-,+), (-,-), (+,-) ----
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// opposite direction: 1<->3, 2<->4, 5<->7, 6<->8
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+template <typename R>
+__host__ __device__ constexpr R w9(int i) {
+    return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+// D2Q5 keeps cs^2 = 1/3 with w0 = 1/3, w1..4 = 1/6
+template <typename R, int Q>
+__host__ __device__ constexpr R wq(int i) {
+    return Q == 5 ? (i == 0 ? R(1) / R(3) : R(1) / R(6)) : w9<R>(i);
+}
+
+// w_i * s with the weight rounding removed.  In FP32 the weights 4/9, 1/9, 1/36
+// all round up by the same 7.45e-9 relative; multiplying by them directly would
+// scale the collided momentum by (1 + 7.45e-9 w_g) every step.  Splitting
+// w_i = hi + lo and fusing s*hi + (s*lo) rounds s*w_i once, without the bias.
+__device__ __forceinline__ float w9_times(int i, float s) {
+    const float hi = w9<float>(i);
+    const float lo = (float)(w9<double>(i) - (double)hi);
+    return __fmaf_rn(s, hi, s * lo);
+}
+__device__ __forceinline__ double w9_times(int i, double s) { return w9<double>(i) * s; }
+// (3/5) * s, rounded once: the pressure of Eq. (32b) feeds the next equilibrium,
+// so a biased 3/5 would compound by ~4e-8 per step in FP32
+__device__ __forceinline__ float three_fifths(float s) {
+    return __fmaf_rn(s, 0.6f, s * (float)(0.6 - (double)0.6f));
+}
+__device__ __forceinline__ double three_fifths(double s) { return 0.6 * s; }
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+template <typename T>
+__device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
+
+// Node coordinate seen by a stencil: periodic wrap, or the mirror ghost of
+// a half-way wall (the ghost takes the value of the adjacent fluid node).
+__device__ __forceinline__ int resolve(int v, int n, int wall) {
+    if (wall) return v < 0 ? 0 : (v >= n ? n - 1 : v);
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Element offset of value q = 0 of node (x, y) in a buffer with NQ values per node.
+template <int NQ>
+__device__ __forceinline__ long long node_off(const Geometry& g, int x, int y) {
+    return ((long long)y * g.nxb + (x >> 5)) * (NQ * 32) + (x & 31);
+}
+
+// Populations per node: 9 f, 9 g, QS h1, QS h2.
+__host__ __device__ constexpr int nq_of(int qs) { return 18 + 2 * qs; }
+
+// Population i of the lattice whose first plane is `plane0`, pulled into node
+// (x, y): the post-collision value of the upstream node x - c_i, or -- if that
+// node is behind a wall -- the node's own value in the opposite direction
+// (half-way bounce-back).  Any node; used off the fast path.
+template <int NQ, typename T, typename R>
+__device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry& g, int x, int y,
+                                      int plane0, int i) {
+    int sx = x - cx(i), sy = y - cy(i);
+    const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+    if ((ox && g.wall_x) || (oy && g.wall_y))
+        return R(ldg(src + node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32));
+    if (ox) sx += sx < 0 ? g.nx : -g.nx;
+    if (oy) sy += sy < 0 ? g.ny : -g.ny;
+    return R(ldg(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
+}
+
+// omp = 1 - phi, passed separately so that it keeps full precision near phi = 1
+template <typename R>
+__device__ __forceinline__ R mixed_diffusivity(const Coeffs<R>& C, R phi, R omp) {
+    const R den = C.KD1 * omp + C.D2 * phi;  // Eq. (18)
+    return den > R(0) ? C.D1D2 / den : R(0);
+}
+
+// Eq. (37): c1 = P1 + (A D_m / 2)[K c2 phi - c1 (1 - phi)], c2 symmetric.
+// With a = A D_m / 2, a1 = a (1 - phi), a2 = a K phi and P = P1 + P2:
+//   c1 = (P1 + a2 P) / (1 + a1 + a2),  c2 = (P2 + a1 P) / (1 + a1 + a2).
+template <typename R>
+__device__ __forceinline__ void solve_scalars(const Coeffs<R>& C, R phi, R omp, R P1, R P2, R& c1,
+                                              R& c2) {
+    const R a = C.halfA * mixed_diffusivity(C, phi, omp);
+    const R a1 = a * omp, a2 = a * C.K * phi;
+    const R P = P1 + P2;
+    const R inv = R(1) / (R(1) + a1 + a2);
+    c1 = (P1 + a2 * P) * inv;
+    c2 = (P2 + a1 * P) * inv;
+}
+
+template <typename R>
+__device__ __forceinline__ R clip01(R v) { return v < R(0) ? R(0) : (v > R(1) ? R(1) : v); }
+
+__device__ __forceinline__ float exp_r(float v) { return expf(v); }
+__device__ __forceinline__ double exp_r(double v) { return exp(v); }
+__device__ __forceinline__ float sqrt_r(float v) { return sqrtf(v); }
+__device__ __forceinline__ double sqrt_r(double v) { return sqrt(v); }
+
+template <typename R>
+__device__ __forceinline__ R viscosity(const Coeffs<R>& C, R phi, R c1, R c2) {
+    const R mu_lin = C.mu2 + C.dmu * clip01(phi);
+    if (C.visc_model == 1) return exp_r(c1 * C.log_mu1 + c2 * C.log_mu2);    // Eq. (48)
+    if (C.visc_model == 2) return mu_lin * exp_r(-C.visc_beta * (c1 + c2));
+    return mu_lin;                                                          // Eq. (7)
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite5(R a, R b, R c, R d, R e) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e);
+}
+
+// Phase-field storage.  FP32 runs keep the f populations as int32 fixed point,
+// F_i = (f_i - w_i / 2) * 2^31, so that their sum is Phi = (phi - 1/2) * 2^31
+// (phi in (-1/2, 3/2)): phi = sum f and the stencils of phi are then exact
+// integer sums, the collision only rounds the small change f* - f (to 2^-31),
+// and sum(phi) is conserved bit for bit.  FP64 runs store f as double.
+template <typename T>
+struct PhaseFix { static constexpr bool on = false; using S = T; };
+template <>
+struct PhaseFix<float> { static constexpr bool on = true; using S = int; };
+constexpr float FIX_ONE = 2147483648.0f;                 // 2^31
+constexpr float FIX_EPS = 4.656612873077392578125e-10f;  // 2^-31
+constexpr double FIX_EPS_D = 4.656612873077392578125e-10;
+
+// Pulled f, h1, h2 of one node (f in its storage form).
+template <typename T, typename R, int QS>
+struct NodeFH {
+    typename PhaseFix<T>::S f[9];
+    R h1[QS], h2[QS];
+};
+
+// Fast pull: interior node at element offset `nd`, upstream offsets `doff`.
+template <int QS, typename T, typename R>
+__device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long long nd,
+                                             const int (&doff)[9], NodeFH<T, R, QS>& P) {
+    using FS = typename PhaseFix<T>::S;
+    const FS* fsrc = reinterpret_cast<const FS*>(src);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P.f[i] = ldg(fsrc + nd + doff[i] + i * 32);
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+        P.h1[i] = R(ldg(src + nd + doff[i] + (18 + i) * 32));
+        P.h2[i] = R(ldg(src + nd + doff[i] + (18 + QS + i) * 32));
+    }
+}
+
+template <int QS, typename T, typename R>
+__device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geometry& g, int x,
+                                            int y, NodeFH<T, R, QS>& P) {
+    constexpr int NQ = nq_of(QS);
+    using FS = typename PhaseFix<T>::S;
+    const FS* fsrc = reinterpret_cast<const FS*>(src);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P.f[i] = pull_any<NQ, FS, FS>(fsrc, g, x, y, 0, i);
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+        P.h1[i] = pull_any<NQ, T, R>(src, g, x, y, 18, i);
+        P.h2[i] = pull_any<NQ, T, R>(src, g, x, y, 18 + QS, i);
+    }
+}
+
+// phi in storage form (exact integer sum for fixed point) and as a number
+template <typename T, typename R, int QS>
+__device__ __forceinline__ typename PhaseFix<T>::S phase_sum(const NodeFH<T, R, QS>& P) {
+    return ((P.f[0] + (P.f[1] + P.f[3])) + (P.f[2] + P.f[4])) + ((P.f[5] + P.f[7]) + (P.f[6] + P.f[8]));
+}
+// phi and 1 - phi from the stored form; in fixed point each is formed as an
+// exact integer before the conversion, so phi is exact to float precision
+// near 0 and 1 - phi near 1
+template <typename T, typename R>
+__device__ __forceinline__ R phase_value(typename PhaseFix<T>::S v) {
+    if constexpr (PhaseFix<T>::on) return R((long long)v + (1LL << 30)) * R(FIX_EPS);
+    else return R(v);
+}
+template <typename T, typename R>
+__device__ __forceinline__ R phase_omp(typename PhaseFix<T>::S v) {
+    if constexpr (PhaseFix<T>::on) return R((1LL << 30) - (long long)v) * R(FIX_EPS);
+    else return R(1) - R(v);
+}
+template <typename T>
+__device__ __forceinline__ double phase_value_d(typename PhaseFix<T>::S v) {
+    if constexpr (PhaseFix<T>::on) return double(v) * FIX_EPS_D + 0.5;
+    else return double(v);
+}
+
+template <typename T, typename R, int QS>
+__device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS>& P,
+                                       typename PhaseFix<T>::S& phis, R& phi, R& c1, R& c2) {
+    phis = phase_sum<T, R, QS>(P);
+    phi = phase_value<T, R>(phis);
+    const R omp = phase_omp<T, R>(phis);
+    R P1 = R(0), P2 = R(0);
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+        P1 += P.h1[i];
+        P2 += P.h2[i];
+    }
+    solve_scalars(C, phi, omp, P1, P2, c1, c2);
+}
+
+// D2Q9 stencils of phi at the ring centre column X (Eqs. 41-42).  Fixed-point
+// phi: the differences and the Laplacian's sums are exact integers, converted
+// once; the cubic of Eq. (4) gets the low bits of phi through its derivative.
+template <typename T, typename R>
+struct PhiStencil {
+    R phi, omp, dx, dy, lap, bulk;  // omp = 1 - phi, bulk = phi (phi - 1)(phi - 1/2)
+};
+
+template <typename T, typename R, int W2>
+__device__ __forceinline__ PhiStencil<T, R> phi_stencil(const typename PhaseFix<T>::S (*rs),
+                                                        const typename PhaseFix<T>::S (*r0),
+                                                        const typename PhaseFix<T>::S (*rn), int X) {
+    PhiStencil<T, R> o;
+    if constexpr (PhaseFix<T>::on) {
+        const int c = r0[X];
+        const int e = r0[X + 1] - c, w = r0[X - 1] - c, n = rn[X] - c, s = rs[X] - c;
+        const int ne = rn[X + 1] - c, nw = rn[X - 1] - c, sw = rs[X - 1] - c, se = rs[X + 1] - c;
+        o.dx = R(e - w) * R(FIX_EPS / 3.0f) + R((ne - nw) + (se - sw)) * R(FIX_EPS / 12.0f);
+        o.dy = R(n - s) * R(FIX_EPS / 3.0f) + R((ne - se) + (nw - sw)) * R(FIX_EPS / 12.0f);
+        const long long ax = (long long)e + w + n + s, dg = (long long)ne + nw + sw + se;
+        o.lap = R(ax) * R(FIX_EPS * (2.0f / 3.0f)) + R(dg) * R(FIX_EPS / 6.0f);
+        // phi, 1 - phi and phi - 1/2 = c 2^-31 are each exact to float precision
+        // where they are small, so the cubic as their product has no cancellation
+        o.phi = phase_value<T, R>(c);
+        o.omp = phase_omp<T, R>(c);
+        o.bulk = -(o.phi * o.omp) * (R(c) * R(FIX_EPS));
+    } else {
+        const R c = r0[X];
+        const R e = r0[X + 1] - c, w = r0[X - 1] - c, n = rn[X] - c, s = rs[X] - c;
+        const R ne = rn[X + 1] - c, nw = rn[X - 1] - c, sw = rs[X - 1] - c, se = rs[X + 1] - c;
+        o.dx = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
+        o.dy = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
+        o.lap = ((e + w) + (n + s)) * R(2.0 / 3.0) + ((ne + nw) + (sw + se)) * R(1.0 / 6.0);
+        o.phi = c;
+        o.omp = R(1) - c;
+        o.bulk = c * (c - R(1)) * (c - R(0.5));
+    }
+    return o;
+}
+
+// Post-collision f of one node: f*_i = (1 - w_f) f_i + w_i (w_f phi + c_i . B)
+// (Eqs. 23-25 with f^eq and F_i gathered).  The rest population takes
+// phi - sum_{i>0} f*_i, so sum f* = phi exactly.
+template <typename T, typename R>
+__device__ __forceinline__ void collide_f(T* __restrict__ o, const typename PhaseFix<T>::S (&f)[9],
+                                          typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By) {
+    if constexpr (PhaseFix<T>::on) {
+        // f*_i - f_i = w_f (w_i phi - f_i) + w_i c_i . B.  In the offset encoding
+        // w_i phi - f_i = w_i Phi - F_i (the w_i / 2 offsets cancel), with
+        // w_i Phi = Phi / 9 or Phi / 36 in integers
+        const int q9 = (int)(((long long)phis * 477218588LL + (1LL << 31)) >> 32);   // Phi / 9
+        const int q36 = (int)(((long long)phis * 119304647LL + (1LL << 31)) >> 32);  // Phi / 36
+        int* oi = reinterpret_cast<int*>(o);
+        const R sc = omega * R(FIX_EPS);
+        int sum = 0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int neq = (i <= 4 ? q9 : q36) - f[i];
+            const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
+            const R d = sc * R(neq) + w9<R>(i) * cB;
+            const int v = f[i] + __float2int_rn(d * R(FIX_ONE));
+            sum += v;
+            stcs(oi + i * 32, v);
+        }
+        stcs(oi, phis - sum);
+    } else {
+        const R a0 = omega * phi, keep = R(1) - omega;
+        R sum = R(0);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
+            const T vs = T(keep * R(f[i]) + w9<R>(i) * (a0 + cB));
+            sum += R(vs);
+            stcs(o + i * 32, vs);
+        }
+        stcs(o, T(phi - sum));
+    }
+}
+
+// The fused step (FIELDS = false) or the macroscopic-field evaluation of the
+// current state (FIELDS = true).
+template <typename T, typename R, int QS, bool FIELDS>
+__global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
+    strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
+                 Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
+                 int out_f64) {
+    constexpr int NQ = nq_of(QS);
+    constexpr int W2 = STRIP_W + 2;
+    using PS = typename PhaseFix<T>::S;
+    __shared__ PS s_phi[4][W2];
+    __shared__ R s_c[4][2][W2];
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int x0 = blockIdx.x * STRIP_W;
+    const int x = x0 + tid;
+    const int ya = blockIdx.y * g.strip_h;
+    const int yb = min(ya + g.strip_h, g.ny);
+    const bool col_in = x < g.nx;
+    const int rx = col_in ? x : resolve(x, g.nx, g.wall_x);
+    const bool x_inner = col_in && x >= 1 && x <= g.nx - 2;
+    const bool halo = tid == 0 || tid == STRIP_W - 1;
+    const int hx = tid == 0 ? resolve(x0 - 1, g.nx, g.wall_x) : resolve(x0 + STRIP_W, g.nx, g.wall_x);
+    const int hcol = tid == 0 ? 0 : STRIP_W + 1;
+
+    // upstream offsets of an interior node (element units, relative to the node)
+    const int row = g.nxb * NQ * 32;
+    const int xm = lane == 0 ? 31 - NQ * 32 : -1;  // node x - 1
+    const int xp = lane == 31 ? NQ * 32 - 31 : 1;  // node x + 1
+    int doff[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) doff[i] = -cy(i) * row + (cx(i) == 1 ? xm : (cx(i) == -1 ? xp : 0));
+
+    // zeroth moments of row yy into ring slot yy & 3; the pulled pops go to P
+    auto moments_row = [&](int yy, NodeFH<T, R, QS>& P) {
+        const int ry = resolve(yy, g.ny, g.wall_y);
+        PS phis;
+        R phi, c1, c2;
+        if (x_inner && ry >= 1 && ry <= g.ny - 2)
+            pull_fh_fast<QS, T, R>(src, node_off<NQ>(g, x, ry), doff, P);
+        else
+            pull_fh_any<QS, T, R>(src, g, rx, ry, P);
+        zeroth<T, R, QS>(C, P, phis, phi, c1, c2);
+        s_phi[yy & 3][tid + 1] = phis;
+        s_c[yy & 3][0][tid + 1] = c1;
+        s_c[yy & 3][1][tid + 1] = c2;
+        if (halo) {
+            NodeFH<T, R, QS> hp;
+            PS hs;
+            R a, b, c;
+            pull_fh_any<QS, T, R>(src, g, hx, ry, hp);
+            zeroth<T, R, QS>(C, hp, hs, a, b, c);
+            s_phi[yy & 3][hcol] = hs;
+            s_c[yy & 3][0][hcol] = b;
+            s_c[yy & 3][1][hcol] = c;
+        }
+    };
+
+    NodeFH<T, R, QS> cur;
+    moments_row(ya - 1, cur);
+    moments_row(ya, cur);
+
+    for (int y = ya; y < yb; ++y) {
+        const bool inner = x_inner && y >= 1 && y <= g.ny - 2;
+        const long long nd = node_off<NQ>(g, x, y);
+        // ---- a. loads of row y: g (pulled) and the previous-step macros ----
+        R gp[9], pv[5];
+        if (col_in) {
+            if (inner) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) gp[i] = R(ldg(src + nd + doff[i] + (9 + i) * 32));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) gp[i] = pull_any<NQ, T, R>(src, g, x, y, 9, i);
+            }
+            if constexpr (!FIELDS) {
+                const R* pp = prev + node_off<5>(g, x, y);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) pv[k] = pp[k * 32];
+            }
+        }
+        // ---- b. zeroth moments of row y+1 (f, h1, h2 pulled once per node) ----
+        NodeFH<T, R, QS> nxt;
+        moments_row(y + 1, nxt);
+        __syncthreads();
+
+        if (col_in) {
+            // ---- c. stencils (Eqs. 41-42, D2Q9 weights) from the shared ring ----
+            const int X = tid + 1;
+            const PhiStencil<T, R> st = phi_stencil<T, R, W2>(s_phi[(y - 1) & 3], s_phi[y & 3],
+                                                              s_phi[(y + 1) & 3], X);
+            const R phi = st.phi, omp = st.omp, dphix = st.dx, dphiy = st.dy, lap = st.lap;
+            const R(*rs)[W2] = s_c[(y - 1) & 3];
+            const R(*r0)[W2] = s_c[y & 3];
+            const R(*rn)[W2] = s_c[(y + 1) & 3];
+            const R c1 = r0[0][X], c2 = r0[1][X];
+            R dc1x, dc1y, dc2x, dc2y;
+            {
+                const R e = r0[0][X + 1], w = r0[0][X - 1], n = rn[0][X], s = rs[0][X];
+                const R ne = rn[0][X + 1], nw = rn[0][X - 1], sw = rs[0][X - 1], se = rs[0][X + 1];
+                dc1x = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
+                dc1y = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
+            }
+            {
+                const R e = r0[1][X + 1], w = r0[1][X - 1], n = rn[1][X], s = rs[1][X];
+                const R ne = rn[1][X + 1], nw = rn[1][X - 1], sw = rs[1][X - 1], se = rs[1][X + 1];
+                dc2x = (e - w) * R(1.0 / 3.0) + ((ne - nw) + (se - sw)) * R(1.0 / 12.0);
+                dc2y = (n - s) * R(1.0 / 3.0) + ((ne - se) + (nw - sw)) * R(1.0 / 12.0);
+            }
+
+            // ---- d. flow macros ----
+            const R phic = clip01(phi);
+            const R rho = C.rho2 + C.drho * phic;                                   // Eq. (6)
+            const R mu_phi = C.beta4 * st.bulk - C.kappa * lap;                     // Eq. (4)
+            const R Fx = mu_phi * dphix + ((rho - C.g_rho_ref) * C.gx + C.Fx);     // F_s + G
+            const R Fy = mu_phi * dphiy + ((rho - C.g_rho_ref) * C.gy + C.Fy);
+            const R jx = (gp[1] - gp[3]) + ((gp[5] - gp[7]) + (gp[8] - gp[6]));
+            const R jy = (gp[2] - gp[4]) + ((gp[5] - gp[7]) + (gp[6] - gp[8]));
+            const R gs = ((gp[1] + gp[3]) + (gp[2] + gp[4])) + ((gp[5] + gp[7]) + (gp[6] + gp[8]));
+            const R inv_rho = R(1) / rho;
+            const R ux = (jx + R(0.5) * Fx) * inv_rho;                              // Eq. (32a)
+            const R uy = (jy + R(0.5) * Fy) * inv_rho;
+            const R uu = ux * ux + uy * uy;
+            // Eq. (32b): cs^2/(1-w0) = 3/5, s_0(u) = -w0 u.u/(2 cs^2) = -(2/3) u.u
+            const R p = three_fifths(gs + R(0.5) * C.drho * (ux * dphix + uy * dphiy) - R(2.0 / 3.0) * rho * uu);
+            const R mu = viscosity<R>(C, phi, c1, c2);
+
+            if constexpr (FIELDS) {
+                const size_t o = (size_t)y * g.nx + x, nn = (size_t)g.nx * g.ny;
+                const R vals[8] = {phi, ux, uy, p, c1, c2, rho, mu};
+                int j = 0;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    if (mask & (1u << b)) {
+                        if (b == 0) {  // phi exactly as stored
+                            const double v = phase_value_d<T>(s_phi[y & 3][X]);
+                            if (out_f64) static_cast<double*>(out)[j * nn + o] = v;
+                            else static_cast<float*>(out)[j * nn + o] = float(v);
+                        } else if (out_f64) {
+                            static_cast<double*>(out)[j * nn + o] = double(vals[b]);
+                        } else {
+                            static_cast<float*>(out)[j * nn + o] = float(vals[b]);
+                        }
+                        ++j;
+                    }
+                }
+            } else {
+                const R omega_g = R(1) / (R(3) * mu * inv_rho + R(0.5));  // Eq. (33): 1/tau_g
+                const R force_g = R(1) - R(0.5) * omega_g;
+
+                // backward differences against the previous step's macros
+                const R dpux = phi * ux - pv[0] * pv[1], dpuy = phi * uy - pv[0] * pv[2];
+                const R d1ux = c1 * ux - pv[3] * pv[1], d1uy = c1 * uy - pv[3] * pv[2];
+                const R d2ux = c2 * ux - pv[4] * pv[1], d2uy = c2 * uy - pv[4] * pv[2];
+                {
+                    R* pp = prev + node_off<5>(g, x, y);
+                    pp[0] = phi;
+                    pp[32] = ux;
+                    pp[64] = uy;
+                    pp[96] = c1;
+                    pp[128] = c2;
+                }
+                // non-finite values, or phi outside the fixed-point range
+                if (!finite5(phi, ux, uy, c1, c2) || !(phi > R(-1.5) && phi < R(1.5))) atomicOr(flag, 1u);
+
+                // unit normal (Eq. 1), regularised
+                const R inv_norm = R(1) / (sqrt_r(dphix * dphix + dphiy * dphiy) + R(1e-4));
+                const R nxv = dphix * inv_norm, nyv = dphiy * inv_norm;
+                T* o = dst + nd;
+
+                // ---- e1. f (Eqs. 23-25) ----
+                {
+                    const R sharp = C.force_f * C.four_over_W * phi * omp;
+                    const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
+                    const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
+                    collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By);
+                }
+                // ---- e2. g (Eqs. 28-31) ----
+                {
+                    const R alpha = omega_g * (R(3) * p - R(1.5) * rho * uu);
+                    const R Vx = R(3) * (omega_g * rho * ux + force_g * Fx);
+                    const R Vy = R(3) * (omega_g * rho * uy + force_g * Fy);
+                    const R gam = R(4.5) * omega_g * rho;
+                    const R del = R(3) * force_g * C.drho;
+                    const R keep = R(1) - omega_g;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const R cu = (cx(i) ? R(cx(i)) * ux : R(0)) + (cy(i) ? R(cy(i)) * uy : R(0));
+                        const R cg = (cx(i) ? R(cx(i)) * dphix : R(0)) + (cy(i) ? R(cy(i)) * dphiy : R(0));
+                        const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
+                        R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
+                        if (i == 0) v -= R(3) * omega_g * p;
+                        stcs(o + (9 + i) * 32, T(v));
+                    }
+                }
+                // ---- e3. h1, h2 (Eqs. 34-36) ----
+                {
+                    const R Dm = mixed_diffusivity(C, phi, omp);
+                    const R S1 = C.A * Dm * (C.K * c2 * phi - c1 * omp);
+                    const R Ht = Dm * (dphix * (dc1x + C.K * dc2x) + dphiy * (dc1y + C.K * dc2y));
+                    const R t1 = C.force_h1 * C.four_over_W * omp * c1;
+                    const R t2 = C.force_h2 * C.four_over_W * phi * c2;
+                    const R a1 = C.omega_h1 * c1 + C.force_h1 * S1 - Ht;
+                    const R a2 = C.omega_h2 * c2 - C.force_h2 * S1 + Ht;
+                    const R B1x = (R(3) * (C.omega_h1 * c1 * ux + C.force_h1 * d1ux) + t1 * nxv);
+                    const R B1y = (R(3) * (C.omega_h1 * c1 * uy + C.force_h1 * d1uy) + t1 * nyv);
+                    const R B2x = (R(3) * (C.omega_h2 * c2 * ux + C.force_h2 * d2ux) - t2 * nxv);
+                    const R B2y = (R(3) * (C.omega_h2 * c2 * uy + C.force_h2 * d2uy) - t2 * nyv);
+                    const R k1 = R(1) - C.omega_h1, k2 = R(1) - C.omega_h2;
+                    R P1 = R(0), P2 = R(0), s1 = R(0), s2 = R(0);
+#pragma unroll
+                    for (int i = 0; i < QS; ++i) {
+                        P1 += cur.h1[i];
+                        P2 += cur.h2[i];
+                    }
+#pragma unroll
+                    for (int i = 1; i < QS; ++i) {
+                        const R w = wq<R, QS>(i);
+                        const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
+                        const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
+                        const T v1 = T(k1 * cur.h1[i] + w * (a1 + c1B));
+                        const T v2 = T(k2 * cur.h2[i] + w * (a2 + c2B));
+                        s1 += R(v1);
+                        s2 += R(v2);
+                        stcs(o + (18 + i) * 32, v1);
+                        stcs(o + (18 + QS + i) * 32, v2);
+                    }
+                    // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
+                    // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
+                    // without c1 they cannot inherit its rounding, and P1 + P2 is kept
+                    stcs(o + 18 * 32, T((P1 + (S1 - Ht)) - s1));
+                    stcs(o + (18 + QS) * 32, T((P2 - (S1 - Ht)) - s2));
+                }
+            }
+        }
+        cur = nxt;
+    }
+}
+
+// Initial state: populations at their (source-shifted) equilibria, written at
+// the upstream node they will be pulled from, so that the first step's read
+// returns exactly f_i = w_i phi, g_i = 0, h_k,i = w_i (c_k -/+ S/2).
+template <typename T, typename R, int QS>
+__global__ void init_kernel(const double* __restrict__ phi_in, const double* __restrict__ c1_in,
+                            const double* __restrict__ c2_in, T* __restrict__ pop,
+                            R* __restrict__ prev, Geometry g, Coeffs<double> C) {
+    constexpr int NQ = nq_of(QS);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const size_t k = (size_t)y * g.nx + x;
+    const double phi = phi_in[k], c1 = c1_in[k], c2 = c2_in[k];
+    const double S1 = C.A * mixed_diffusivity(C, phi, 1.0 - phi) * (C.K * c2 * phi - c1 * (1.0 - phi));
+    // location that direction i of node (x, y) is pulled from (pre-streamed layout)
+    auto where = [&](int plane0, int i) -> long long {
+        int sx = x - cx(i), sy = y - cy(i);
+        const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+        if ((ox && g.wall_x) || (oy && g.wall_y)) return node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32;
+        if (ox) sx += sx < 0 ? g.nx : -g.nx;
+        if (oy) sy += sy < 0 ? g.ny : -g.ny;
+        return node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
+    };
+    auto put_f = [&](auto* fp, int i, auto v) { fp[where(0, i)] = v; };
+    auto put = [&](int plane0, int i, double v) {
+        int sx = x - cx(i), sy = y - cy(i);
+        const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+        long long at;
+        if ((ox && g.wall_x) || (oy && g.wall_y)) {
+            at = node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32;
+        } else {
+            if (ox) sx += sx < 0 ? g.nx : -g.nx;
+            if (oy) sy += sy < 0 ? g.ny : -g.ny;
+            at = node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
+        }
+        pop[at] = T(v);
+    };
+    using FS = typename PhaseFix<T>::S;
+    FS* fpop = reinterpret_cast<FS*>(pop);
+    for (int i = 0; i < 9; ++i) {
+        const double fi = w9<double>(i) * phi;
+        if constexpr (PhaseFix<T>::on) {
+            // the same rest-population rule as the collision: sum_i F_i = round(phi 2^30)
+            (void)fi;
+        } else {
+            put_f(fpop, i, fi);
+        }
+        put(9, i, 0.0);
+    }
+    if constexpr (PhaseFix<T>::on) {
+        const long long Phi = llrint((phi - 0.5) * 2147483648.0);
+        long long rest = Phi;
+        for (int i = 1; i < 9; ++i) {
+            const long long Fi = llrint(w9<double>(i) * (phi - 0.5) * 2147483648.0);
+            rest -= Fi;
+            put_f(fpop, i, (int)Fi);
+        }
+        put_f(fpop, 0, (int)rest);
+    }
+    for (int i = 0; i < QS; ++i) {
+        put(18, i, wq<double, QS>(i) * (c1 - 0.5 * S1));
+        put(18 + QS, i, wq<double, QS>(i) * (c2 + 0.5 * S1));
+    }
+    R* pp = prev + node_off<5>(g, x, y);
+    pp[0] = R(phi);
+    pp[32] = R(0);
+    pp[64] = R(0);
+    pp[96] = R(c1);
+    pp[128] = R(c2);
+}
+
+// Block partials of {sum phi, sum(c1 + c2)}; c1 + c2 = sum h1 + sum h2 exactly
+// (the two interfacial exchange terms of Eq. 37 cancel).
+template <typename T, int QS>
+__global__ void __launch_bounds__(RED_THREADS)
+    conserved_partials(const T* __restrict__ pop, Geometry g, double* __restrict__ partials) {
+    constexpr int NQ = nq_of(QS);
+    using FS = typename PhaseFix<T>::S;
+    const FS* fp = reinterpret_cast<const FS*>(pop);
+    // fixed point: sum of the integers Phi (exact); otherwise sum of phi
+    long long ai = 0;
+    double a = 0.0, b = 0.0;
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
+        if constexpr (PhaseFix<T>::on) {
+            long long s = 0;
+            for (int i = 0; i < 9; ++i) s += pull_any<NQ, FS, FS>(fp, g, x, y, 0, i);
+            ai += s;
+        } else {
+            for (int i = 0; i < 9; ++i) a += pull_any<NQ, FS, double>(fp, g, x, y, 0, i);
+        }
+        double c = 0.0;
+        for (int i = 0; i < QS; ++i)
+            c += pull_any<NQ, T, double>(pop, g, x, y, 18, i) + pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i);
+        b += c;
+    }
+    __shared__ double sa[RED_THREADS / 32], sb[RED_THREADS / 32];
+    __shared__ long long si[RED_THREADS / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+        ai += __shfl_down_sync(0xffffffffu, ai, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sa[wid] = a; sb[wid] = b; si[wid] = ai; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        long long AI = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) { A += sa[w]; B += sb[w]; AI += si[w]; }
+        partials[2 * blockIdx.x] = PhaseFix<T>::on ? __longlong_as_double(AI) : A;
+        partials[2 * blockIdx.x + 1] = B;
+    }
+}
+
+// Final pass over the block partials in a fixed order (deterministic).  For the
+// fixed-point phase field the integer total is exact and converted once:
+// sum phi = (sum Phi) 2^-31 + n / 2.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    conserved_final(const double* __restrict__ partials, int nblocks, long long nodes,
+                    double* __restrict__ out) {
+    __shared__ double sa[RED_THREADS], sb[RED_THREADS];
+    __shared__ long long si[RED_THREADS];
+    double a = 0.0, b = 0.0;
+    long long ai = 0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        if (PhaseFix<T>::on) ai += __double_as_longlong(partials[2 * k]);
+        else a += partials[2 * k];
+        b += partials[2 * k + 1];
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    si[threadIdx.x] = ai;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+            si[threadIdx.x] += si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = PhaseFix<T>::on ? double(si[0]) * FIX_EPS_D + 0.5 * double(nodes) : sa[0];
+        out[1] = sb[0];
+    }
+}
+
+// ---- launchers ----
+inline dim3 strip_grid(const Geometry& g) {
+    return dim3((g.nx + STRIP_W - 1) / STRIP_W, (g.ny + g.strip_h - 1) / g.strip_h);
+}
+
+template <typename T, typename R>
+cudaError_t launch_step_impl(const void* src, void* dst, void* prev, const Geometry& g,
+                             const Coeffs<R>& C, int q, unsigned* flag, cudaStream_t s) {
+    if (q == 5)
+        strip_kernel<T, R, 5, false><<<strip_grid(g), STRIP_W, 0, s>>>(
+            (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+    else
+        strip_kernel<T, R, 9, false><<<strip_grid(g), STRIP_W, 0, s>>>(
+            (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+    return cudaGetLastError();
+}
+
+template <typename T, typename R>
+cudaError_t launch_fields_impl(const void* src, const Geometry& g, const Coeffs<R>& C, int q,
+                               uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    if (q == 5)
+        strip_kernel<T, R, 5, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+            (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
+    else
+        strip_kernel<T, R, 9, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+            (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
+    return cudaGetLastError();
+}
+
+template <typename T, typename R>
+cudaError_t launch_init_impl(const double* phi, const double* c1, const double* c2, void* pop,
+                             void* prev, const Geometry& g, const Coeffs<double>& C, int q,
+                             cudaStream_t s) {
+    dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
+    if (q == 5)
+        init_kernel<T, R, 5><<<grid, block, 0, s>>>(phi, c1, c2, (T*)pop, (R*)prev, g, C);
+    else
+        init_kernel<T, R, 9><<<grid, block, 0, s>>>(phi, c1, c2, (T*)pop, (R*)prev, g, C);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_conserved_impl(const void* pop, const Geometry& g, int q, double* partials,
+                                  double* out, cudaStream_t s) {
+    if (q == 5)
+        conserved_partials<T, 5><<<RED_BLOCKS, RED_THREADS, 0, s>>>((const T*)pop, g, partials);
+    else
+        conserved_partials<T, 9><<<RED_BLOCKS, RED_THREADS, 0, s>>>((const T*)pop, g, partials);
+    conserved_final<T><<<1, RED_THREADS, 0, s>>>(partials, RED_BLOCKS, (long long)g.nx * g.ny, out);
+    return cudaGetLastError();
+}
+
+template <typename T, typename R>
+int step_blocks_per_sm_impl(int q) {
+    int n = 0;
+    if (q == 5)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, strip_kernel<T, R, 5, false>, STRIP_W, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, strip_kernel<T, R, 9, false>, STRIP_W, 0);
+    return n;
+}
+
+}  // namespace lbm
