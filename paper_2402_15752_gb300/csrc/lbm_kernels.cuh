@@ -113,10 +113,23 @@ __device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry&
 }
 
 // omp = 1 - phi, passed separately so that it keeps full precision near phi = 1
+// FP32 uses the hardware-approximation intrinsics (a few ulp; the parity budget
+// is 1e-5), FP64 the IEEE operations.
+__device__ __forceinline__ float exp_r(float v) { return __expf(v); }
+__device__ __forceinline__ double exp_r(double v) { return exp(v); }
+__device__ __forceinline__ float div_r(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_r(double a, double b) { return a / b; }
+// |(x, y)|
+__device__ __forceinline__ float norm_r(float x, float y) {
+    const float s = x * x + y * y;
+    return s > 0.0f ? s * rsqrtf(s) : 0.0f;
+}
+__device__ __forceinline__ double norm_r(double x, double y) { return sqrt(x * x + y * y); }
+
 template <typename R>
 __device__ __forceinline__ R mixed_diffusivity(const Coeffs<R>& C, R phi, R omp) {
     const R den = C.KD1 * omp + C.D2 * phi;  // Eq. (18)
-    return den > R(0) ? C.D1D2 / den : R(0);
+    return den > R(0) ? div_r(C.D1D2, den) : R(0);
 }
 
 // Eq. (37): c1 = P1 + (A D_m / 2)[K c2 phi - c1 (1 - phi)], c2 symmetric.
@@ -128,18 +141,13 @@ __device__ __forceinline__ void solve_scalars(const Coeffs<R>& C, R phi, R omp, 
     const R a = C.halfA * mixed_diffusivity(C, phi, omp);
     const R a1 = a * omp, a2 = a * C.K * phi;
     const R P = P1 + P2;
-    const R inv = R(1) / (R(1) + a1 + a2);
+    const R inv = div_r(R(1), R(1) + a1 + a2);
     c1 = (P1 + a2 * P) * inv;
     c2 = (P2 + a1 * P) * inv;
 }
 
 template <typename R>
 __device__ __forceinline__ R clip01(R v) { return v < R(0) ? R(0) : (v > R(1) ? R(1) : v); }
-
-__device__ __forceinline__ float exp_r(float v) { return expf(v); }
-__device__ __forceinline__ double exp_r(double v) { return exp(v); }
-__device__ __forceinline__ float sqrt_r(float v) { return sqrtf(v); }
-__device__ __forceinline__ double sqrt_r(double v) { return sqrt(v); }
 
 template <typename R>
 __device__ __forceinline__ R viscosity(const Coeffs<R>& C, R phi, R c1, R c2) {
@@ -343,9 +351,15 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
     const bool col_in = x < g.nx;
     const int rx = col_in ? x : resolve(x, g.nx, g.wall_x);
     const bool x_inner = col_in && x >= 1 && x <= g.nx - 2;
+    // Halo columns: lane 0 (tid 0) takes the right one, x0 + 128, and lane 31
+    // (tid 127) the left one, x0 - 1.  Each halo node then sits at the same
+    // position in its 32-node block as the lane's own node, so it reuses the
+    // lane's upstream offsets on the fast path.
     const bool halo = tid == 0 || tid == STRIP_W - 1;
-    const int hx = tid == 0 ? resolve(x0 - 1, g.nx, g.wall_x) : resolve(x0 + STRIP_W, g.nx, g.wall_x);
-    const int hcol = tid == 0 ? 0 : STRIP_W + 1;
+    const int hraw = tid == 0 ? x0 + STRIP_W : x0 - 1;
+    const int hx = resolve(hraw, g.nx, g.wall_x);
+    const bool h_inner = hraw == hx && hx >= 1 && hx <= g.nx - 2;
+    const int hcol = tid == 0 ? STRIP_W + 1 : 0;
 
     // upstream offsets of an interior node (element units, relative to the node)
     const int row = g.nxb * NQ * 32;
@@ -372,7 +386,10 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
             NodeFH<T, R, QS> hp;
             PS hs;
             R a, b, c;
-            pull_fh_any<QS, T, R>(src, g, hx, ry, hp);
+            if (h_inner && ry >= 1 && ry <= g.ny - 2)
+                pull_fh_fast<QS, T, R>(src, node_off<NQ>(g, hx, ry), doff, hp);
+            else
+                pull_fh_any<QS, T, R>(src, g, hx, ry, hp);
             zeroth<T, R, QS>(C, hp, hs, a, b, c);
             s_phi[yy & 3][hcol] = hs;
             s_c[yy & 3][0][hcol] = b;
@@ -441,7 +458,7 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
             const R jx = (gp[1] - gp[3]) + ((gp[5] - gp[7]) + (gp[8] - gp[6]));
             const R jy = (gp[2] - gp[4]) + ((gp[5] - gp[7]) + (gp[6] - gp[8]));
             const R gs = ((gp[1] + gp[3]) + (gp[2] + gp[4])) + ((gp[5] + gp[7]) + (gp[6] + gp[8]));
-            const R inv_rho = R(1) / rho;
+            const R inv_rho = div_r(R(1), rho);
             const R ux = (jx + R(0.5) * Fx) * inv_rho;                              // Eq. (32a)
             const R uy = (jy + R(0.5) * Fy) * inv_rho;
             const R uu = ux * ux + uy * uy;
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                     }
                 }
             } else {
-                const R omega_g = R(1) / (R(3) * mu * inv_rho + R(0.5));  // Eq. (33): 1/tau_g
+                const R omega_g = div_r(R(1), R(3) * mu * inv_rho + R(0.5));  // Eq. (33): 1/tau_g
                 const R force_g = R(1) - R(0.5) * omega_g;
 
                 // backward differences against the previous step's macros
@@ -488,7 +505,7 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                 if (!finite5(phi, ux, uy, c1, c2) || !(phi > R(-1.5) && phi < R(1.5))) atomicOr(flag, 1u);
 
                 // unit normal (Eq. 1), regularised
-                const R inv_norm = R(1) / (sqrt_r(dphix * dphix + dphiy * dphiy) + R(1e-4));
+                const R inv_norm = div_r(R(1), norm_r(dphix, dphiy) + R(1e-4));
                 const R nxv = dphix * inv_norm, nyv = dphiy * inv_norm;
                 T* o = dst + nd;
 
