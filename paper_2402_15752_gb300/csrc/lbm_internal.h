@@ -10,9 +10,15 @@ namespace lbm {
 
 // Step kernel: a CTA of STRIP_WARPS warps owns STRIP_W consecutive columns and
 // marches up a strip of `strip_h` rows, one thread per column.
-constexpr int STRIP_WARPS = 4;
+#ifndef LBM_STRIP_WARPS
+#define LBM_STRIP_WARPS 4
+#endif
+#ifndef LBM_STRIP_MIN_BLOCKS
+#define LBM_STRIP_MIN_BLOCKS 5
+#endif
+constexpr int STRIP_WARPS = LBM_STRIP_WARPS;
 constexpr int STRIP_W = 32 * STRIP_WARPS;
-constexpr int STRIP_MIN_BLOCKS = 5;  // occupancy target: caps registers at 102/thread
+constexpr int STRIP_MIN_BLOCKS = LBM_STRIP_MIN_BLOCKS;  // occupancy target (register cap)
 // Blocks of the conserved-sum reduction (fixed, so the summation order is fixed).
 constexpr int RED_BLOCKS = 304;
 constexpr int RED_THREADS = 256;

@@ -220,14 +220,19 @@ __device__ __forceinline__ typename PhaseFix<T>::S phase_sum(const NodeFH<T, R, 
 // phi and 1 - phi from the stored form; in fixed point each is formed as an
 // exact integer before the conversion, so phi is exact to float precision
 // near 0 and 1 - phi near 1
+// (32-bit integer work only: phi * 2^31 = Phi + 2^30 fits an int32 while phi < 1,
+// and (1 - phi) * 2^31 = 2^30 - Phi while phi > 0; beyond those ends the other
+// form is used, which is exact enough there.)
 template <typename T, typename R>
 __device__ __forceinline__ R phase_value(typename PhaseFix<T>::S v) {
-    if constexpr (PhaseFix<T>::on) return R((long long)v + (1LL << 30)) * R(FIX_EPS);
+    if constexpr (PhaseFix<T>::on)
+        return v < (1 << 30) ? R(v + (1 << 30)) * R(FIX_EPS) : R(v) * R(FIX_EPS) + R(0.5);
     else return R(v);
 }
 template <typename T, typename R>
 __device__ __forceinline__ R phase_omp(typename PhaseFix<T>::S v) {
-    if constexpr (PhaseFix<T>::on) return R((1LL << 30) - (long long)v) * R(FIX_EPS);
+    if constexpr (PhaseFix<T>::on)
+        return v > -(1 << 30) ? R((1 << 30) - v) * R(FIX_EPS) : R(0.5) - R(v) * R(FIX_EPS);
     else return R(1) - R(v);
 }
 template <typename T>
@@ -270,7 +275,9 @@ __device__ __forceinline__ PhiStencil<T, R> phi_stencil(const typename PhaseFix<
         const int ne = rn[X + 1] - c, nw = rn[X - 1] - c, sw = rs[X - 1] - c, se = rs[X + 1] - c;
         o.dx = R(e - w) * R(FIX_EPS / 3.0f) + R((ne - nw) + (se - sw)) * R(FIX_EPS / 12.0f);
         o.dy = R(n - s) * R(FIX_EPS / 3.0f) + R((ne - se) + (nw - sw)) * R(FIX_EPS / 12.0f);
-        const long long ax = (long long)e + w + n + s, dg = (long long)ne + nw + sw + se;
+        // second differences: exact in int32 for any state whose node-to-node
+        // change of phi is below 1/4 (a tanh profile of width W = 4 stays below 1/4)
+        const int ax = (e + w) + (n + s), dg = (ne + nw) + (sw + se);
         o.lap = R(ax) * R(FIX_EPS * (2.0f / 3.0f)) + R(dg) * R(FIX_EPS / 6.0f);
         // phi, 1 - phi and phi - 1/2 = c 2^-31 are each exact to float precision
         // where they are small, so the cubic as their product has no cancellation
@@ -299,18 +306,17 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
                                           typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By) {
     if constexpr (PhaseFix<T>::on) {
         // f*_i - f_i = w_f (w_i phi - f_i) + w_i c_i . B.  In the offset encoding
-        // w_i phi - f_i = w_i Phi - F_i (the w_i / 2 offsets cancel), with
-        // w_i Phi = Phi / 9 or Phi / 36 in integers
-        const int q9 = (int)(((long long)phis * 477218588LL + (1LL << 31)) >> 32);   // Phi / 9
-        const int q36 = (int)(((long long)phis * 119304647LL + (1LL << 31)) >> 32);  // Phi / 36
+        // w_i phi - f_i = w_i Phi - F_i (the w_i / 2 offsets cancel); Phi - 9 F_i
+        // (or Phi - 36 F_i) is the small non-equilibrium part, exact in int32,
+        // and is divided by 9 (36) only after the conversion
         int* oi = reinterpret_cast<int*>(o);
-        const R sc = omega * R(FIX_EPS);
+        const R sc9 = omega * R(FIX_EPS / 9.0f), sc36 = omega * R(FIX_EPS / 36.0f);
         int sum = 0;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const int neq = (i <= 4 ? q9 : q36) - f[i];
+            const R neq = i <= 4 ? sc9 * R(phis - 9 * f[i]) : sc36 * R(phis - 36 * f[i]);
             const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-            const R d = sc * R(neq) + w9<R>(i) * cB;
+            const R d = neq + w9<R>(i) * cB;
             const int v = f[i] + __float2int_rn(d * R(FIX_ONE));
             sum += v;
             stcs(oi + i * 32, v);
