@@ -56,6 +56,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank number over all ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, cells: int, steps: int, ms_max: float) -> float:
+    """Units processed by all ranks (each runs its own replica) over the slowest rank's time."""
+    return world * cells * steps / (ms_max * 1e-3) / 1e6
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -217,13 +233,6 @@ def run_ours(args, rank, world, local):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     w = make_workload(args.workload)
     sim = Simulation(w.params, precision=args.precision, device=dev)
     sim.init(w.sdf, w.c1_tilde, w.c2_tilde)
@@ -247,9 +256,9 @@ def run_ours(args, rank, world, local):
     barrier()
     clocks = sampler.stop()
     sim.sync()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     cells = w.cells
-    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, cells, args.steps, ms)
 
     # ---- roofline of the fused kernel (the only kernel in the timed region) ----
     q = int(w.params.get("scalar_q", 5))
@@ -277,8 +286,8 @@ def run_ours(args, rank, world, local):
         t1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ems = max_over_ranks(t0.elapsed_time(t1))
-        e2e = {"value": world * cells * args.steps / (ems * 1e-3) / 1e6, "unit": "MLUPS",
+        ems = max_over_ranks(t0.elapsed_time(t1), world, dev)
+        e2e = {"value": whole_job_mlups(world, cells, args.steps, ems), "unit": "MLUPS",
                "h2d_bytes_per_step": cells * 8 / args.steps,
                "d2h_bytes_per_step": 6 * cells * 4 / args.steps}
         sim.sync()
