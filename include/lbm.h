@@ -151,6 +151,34 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_devic
 /* Steps taken since the last init or set_state. */
 int64_t lbm_time(const lbm_handle* h);
 
+/* Conserved sums {sum phi, sum (c1 + c2)} of a solver state that lives in device
+ * memory (the bytes lbm_get_state writes, on the device), without a handle and
+ * without allocating anything.  The paper has no counterpart: this is a service of
+ * the library.
+ * Who needs it: code that must not touch the device allocator -- a monitor or
+ * checkpoint validator running inside a host application whose GPU memory is owned
+ * by another allocator or fully reserved, a process that has run out of device
+ * memory and still has to verify a saved state, or code issued between stream
+ * captures that must not change the memory footprint.  lbm_conserved needs a handle,
+ * and a handle needs a caller workspace; this call needs neither.
+ * Scratch: a fixed array of 131,088 bytes in the library's device data (held by each
+ * GPU that loads the library until the process exits) holds one partial per chunk of
+ * 8192 nodes; grids above 67,108,864 nodes (8192 x 8192) are rejected with
+ * LBM_ERR_ARG.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address (once per device,
+ * under a lock); make that first call before any stream capture on that device.
+ * All calls on a device share the array, so calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race: serialise them.  Every slot a
+ * call reads is written by the same call first.
+ * params: the parameters the state was created with (layout: nx, ny, scalar_q,
+ * precision, boundaries).  d_state: device pointer, state_bytes >= its population
+ * part.  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
+ * host (the call synchronises the stream) or device (out_on_device != 0, asynchronous).
+ * err: optional buffer of err_len bytes for an error message (may be NULL). */
+int lbm_conserved_noalloc(const lbm_params* params, const void* d_state, size_t state_bytes,
+                          void* cuda_stream, double* out, int32_t out_on_device, char* err,
+                          size_t err_len);
+
 /* Release the handle (and its CUDA graphs/events); the workspace stays the caller's. */
 void lbm_destroy(lbm_handle* h);
 
