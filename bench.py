@@ -1,7 +1,7 @@
 """Benchmark of the fused phase-field LB step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload bubble1024x2048|droplets8192] [--precision fp32|fp64]
+                    [--workload bubble1024x2048|droplets8192] [--precision fp32|fp64|bf16|fp16]
 
 One step = one pass of the whole hot path over the grid: pull-streaming of
 f, g, h1, h2, zeroth moments, stencils, flow macros, collision of the four
@@ -43,7 +43,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bubble1024x2048", choices=["bubble1024x2048", "droplets8192"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"],
+                    help="population storage (bf16/fp16: 16-bit storage, FP32 arithmetic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -220,7 +221,7 @@ def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
 
-    from paper_2402_15752_gb300 import Simulation
+    from paper_2402_15752_gb300 import LBMError, Simulation
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py: no CUDA device (the GPU path has no CPU fallback)")
@@ -238,7 +239,15 @@ def run_ours(args, rank, world, local):
     sim.init(w.sdf, w.c1_tilde, w.c2_tilde)
     stream = sim.stream
     sim.step(max(3, args.warmup))
-    sim.sync()
+    try:
+        sim.sync()
+    except LBMError as e:  # a reduced storage precision that cannot carry this flow
+        if rank == 0:
+            print(json.dumps({"metric": "MLUPS", "value": None, "unit": "MLUPS", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "config": {"workload": args.workload, "precision": args.precision},
+                              "failed": "non-finite state during warm-up: %s" % e}))
+        return
 
     # ---- device-timed region: K fused steps, inputs resident in HBM ----
     phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
@@ -255,15 +264,20 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    sim.sync()
+    state_ok = True
+    try:
+        sim.sync()
+    except LBMError:
+        state_ok = False  # timed, but the state went non-finite: flagged in the line
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     cells = w.cells
     value = whole_job_mlups(world, cells, args.steps, ms)
 
     # ---- roofline of the fused kernel (the only kernel in the timed region) ----
     q = int(w.params.get("scalar_q", 5))
-    elem = 8 if args.precision == "fp64" else 4
-    bytes_per_cell = 2 * (18 + 2 * q) * elem + 2 * 5 * elem
+    elem = {"fp64": 8, "fp32": 4}.get(args.precision, 2)  # bytes of a stored population
+    relem = 8 if args.precision == "fp64" else 4          # bytes of a previous-step macro
+    bytes_per_cell = 2 * (18 + 2 * q) * elem + 2 * 5 * relem
     launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_cell * cells / launch_s / 1e9
     peak, peak_kind = hbm_peak()
@@ -271,7 +285,7 @@ def run_ours(args, rank, world, local):
 
     # ---- end to end through the public API, host buffers, copies timed ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and state_ok:
         sdf_host = torch.from_numpy(np.ascontiguousarray(w.sdf, dtype=np.float64)).pin_memory()
         out_host = torch.empty((6, w.params["ny"], w.params["nx"]), dtype=torch.float32).pin_memory()
         names = ("phi", "ux", "uy", "p", "c1", "c2")
@@ -305,7 +319,7 @@ def run_ours(args, rank, world, local):
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "nx": w.params["nx"], "ny": w.params["ny"],
                        "bc": "walls" if w.params["wall_x"] else "periodic", "scalar_q": q,
                        "precision": args.precision, "l2": "state larger than L2 (no flush)",
@@ -318,6 +332,8 @@ def run_ours(args, rank, world, local):
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if not state_ok:
+            line["failed"] = "the state went non-finite during the timed steps"
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:

@@ -52,6 +52,16 @@ extern "C" {
 
 #define LBM_FP64           0 /* FP64 storage and arithmetic                      */
 #define LBM_FP32           1 /* FP32 storage and arithmetic                      */
+/* 16-bit population storage, FP32 arithmetic: each population is read, converted
+ * and collided in FP32 and rounded stochastically on the store (deterministic
+ * hash bits, so runs and restarts are reproducible).  f is stored as the offset
+ * f_i - w_i/2 from its value at phi = 1/2, g as it is (bfloat16) or as g_i * 2^10
+ * (half), h as it is; the five previous-step macros stay FP32.  Not in the paper:
+ * it halves the population bytes per node (112 -> 56 for scalar_q = 5) at a field
+ * error of 1e-3..1e-2 (half); bfloat16 cannot carry density ratios near 1000. */
+#define LBM_FP32_BF16STORE 2 /* bfloat16 storage (8-bit significand, FP32 range)  */
+#define LBM_FP32_FP16STORE 3 /* IEEE half storage (11-bit significand, |x| < 65504;
+                                values below 6.1e-5 lose bits as subnormals)        */
 
 #define LBM_VISC_LINEAR 0 /* mu = phi (mu1 - mu2) + mu2                 Eq. (7)  */
 #define LBM_VISC_LOG_C  1 /* log mu = c1 log mu1 + c2 log mu2          Eq. (48) */
@@ -80,7 +90,7 @@ typedef struct {
     int32_t nx, ny;        /* grid nodes, each >= 1                                  */
     int32_t bc_x, bc_y;    /* LBM_BC_PERIODIC or LBM_BC_WALL                         */
     int32_t scalar_q;      /* 5 (D2Q5) or 9 (D2Q9) for h1, h2                        */
-    int32_t precision;     /* LBM_FP64 or LBM_FP32                                   */
+    int32_t precision;     /* LBM_FP64, LBM_FP32, LBM_FP32_BF16STORE or LBM_FP32_FP16STORE */
     double W, M, sigma;    /* interface width, mobility, surface tension (> 0, > 0, >= 0) */
     double rho1, rho2;     /* densities (> 0)                                        */
     double mu1, mu2;       /* dynamic viscosities (> 0)                              */
@@ -96,8 +106,9 @@ typedef struct {
 typedef struct lbm_handle lbm_handle;
 
 /* Bytes of device workspace the parameters need (0 if the parameters are invalid).
- * Layout per node: two population buffers (28 values for scalar_q = 5, 36 for 9),
- * five previous-step macros, plus a few KB of reduction partials and flags. */
+ * Layout per node: two population buffers (28 values for scalar_q = 5, 36 for 9, of
+ * 8, 4 or 2 bytes), five previous-step macros (8 bytes for LBM_FP64, else 4), plus a
+ * few KB of reduction partials and flags. */
 size_t lbm_workspace_bytes(const lbm_params* params);
 
 /* Validate parameters (Sec. III relaxation-time relations: every tau > 1/2),

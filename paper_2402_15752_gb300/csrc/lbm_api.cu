@@ -10,6 +10,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <type_traits>
 
 namespace {
 
@@ -41,7 +42,7 @@ int validate(const lbm_params* p, char* err, size_t n) {
         snprintf(err, n, "bc_x/bc_y must be LBM_BC_PERIODIC or LBM_BC_WALL"); return LBM_ERR_ARG;
     }
     if (p->scalar_q != 5 && p->scalar_q != 9) { snprintf(err, n, "scalar_q must be 5 or 9 (got %d)", p->scalar_q); return LBM_ERR_ARG; }
-    if (p->precision != LBM_FP64 && p->precision != LBM_FP32) { snprintf(err, n, "unknown precision %d", p->precision); return LBM_ERR_ARG; }
+    if (p->precision < LBM_FP64 || p->precision > LBM_FP32_FP16STORE) { snprintf(err, n, "unknown precision %d", p->precision); return LBM_ERR_ARG; }
     if (p->visc_model < LBM_VISC_LINEAR || p->visc_model > LBM_VISC_EXP_T) { snprintf(err, n, "unknown visc_model %d", p->visc_model); return LBM_ERR_ARG; }
     if (!finite_pos(p->W)) { snprintf(err, n, "W must be > 0"); return LBM_ERR_ARG; }
     if (!finite_pos(p->rho1) || !finite_pos(p->rho2)) { snprintf(err, n, "rho1, rho2 must be > 0"); return LBM_ERR_ARG; }
@@ -59,8 +60,8 @@ int validate(const lbm_params* p, char* err, size_t n) {
 Layout layout_of(const lbm_params* p) {
     Layout L;
     L.nq = 18 + 2 * p->scalar_q;  // f, g, h1, h2
-    L.elem = p->precision == LBM_FP64 ? 8 : 4;
-    L.relem = p->precision == LBM_FP64 ? 8 : 4;
+    L.elem = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP32 ? 4 : 2);
+    L.relem = p->precision == LBM_FP64 ? 8 : 4;  // previous-step macros: arithmetic type
     L.nxb = (p->nx + 31) / 32;
     L.pop_elems = (size_t)p->ny * L.nxb * L.nq * 32;
     L.prev_elems = (size_t)p->ny * L.nxb * 5 * 32;
@@ -154,7 +155,6 @@ struct lbm_handle {
     double* partials() const { return reinterpret_cast<double*>(ws + L.off_part); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(ws + L.off_misc); }
     double* sums() const { return reinterpret_cast<double*>(ws + L.off_misc + 16); }
-    bool f64() const { return p.precision == LBM_FP64; }
 
     int fail(int code, const char* what, cudaError_t e = cudaSuccess) {
         if (e != cudaSuccess) snprintf(err, sizeof(err), "%s: %s", what, cudaGetErrorString(e));
@@ -162,16 +162,26 @@ struct lbm_handle {
         return code;
     }
 
+    template <typename R>
+    const lbm::Coeffs<R>& coeffs() const {
+        if constexpr (std::is_same<R, double>::value) return cd;
+        else return cf;
+    }
+
     cudaError_t step_once(int from, cudaStream_t s) {
-        if (f64())
-            return lbm::launch_step<double, double>(pop(from), pop(from ^ 1), prev(), geo, cd, p.scalar_q, flag(), s);
-        return lbm::launch_step<float, float>(pop(from), pop(from ^ 1), prev(), geo, cf, p.scalar_q, flag(), s);
+        return lbm::by_storage(p.precision, [&](auto t, auto r) {
+            using T = decltype(t);
+            using R = decltype(r);
+            return lbm::launch_step<T, R>(pop(from), pop(from ^ 1), prev(), geo, coeffs<R>(), p.scalar_q, flag(), s);
+        });
     }
 
     cudaError_t fields(int from, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
-        if (f64())
-            return lbm::launch_fields<double, double>(pop(from), geo, cd, p.scalar_q, mask, out, out_f64, s);
-        return lbm::launch_fields<float, float>(pop(from), geo, cf, p.scalar_q, mask, out, out_f64, s);
+        return lbm::by_storage(p.precision, [&](auto t, auto r) {
+            using T = decltype(t);
+            using R = decltype(r);
+            return lbm::launch_fields<T, R>(pop(from), geo, coeffs<R>(), p.scalar_q, mask, out, out_f64, s);
+        });
     }
 
     cudaError_t build_graph(int parity) {
@@ -205,8 +215,9 @@ struct lbm_handle {
 static int choose_strip_height(const lbm_handle* h) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms <= 0) sms = 1;
-    int per_sm = h->f64() ? lbm::step_blocks_per_sm<double, double>(h->p.scalar_q)
-                          : lbm::step_blocks_per_sm<float, float>(h->p.scalar_q);
+    int per_sm = lbm::by_storage(h->p.precision, [&](auto t, auto r) {
+        return lbm::step_blocks_per_sm<decltype(t), decltype(r)>(h->p.scalar_q);
+    });
     cudaGetLastError();
     if (per_sm <= 0) per_sm = 1;
     const long long slots = (long long)sms * per_sm;
@@ -284,11 +295,10 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
 }
 
 static int init_common(lbm_handle* h, const double* phi, const double* c1, const double* c2) {
-    cudaError_t e;
-    if (h->f64())
-        e = lbm::launch_init<double, double>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd, h->p.scalar_q, h->stream);
-    else
-        e = lbm::launch_init<float, float>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd, h->p.scalar_q, h->stream);
+    cudaError_t e = lbm::by_storage(h->p.precision, [&](auto t, auto r) {
+        return lbm::launch_init<decltype(t), decltype(r)>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd,
+                                                          h->p.scalar_q, h->stream);
+    });
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "init kernel", e);
     h->cur = 0;
@@ -410,9 +420,10 @@ int lbm_conserved(lbm_handle* h, double out[2]) {
     if (!h) return LBM_ERR_ARG;
     if (!out) return h->fail(LBM_ERR_ARG, "out is NULL");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->f64()
-        ? lbm::launch_conserved<double>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(), h->stream)
-        : lbm::launch_conserved<float>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(), h->stream);
+    cudaError_t e = lbm::by_storage(h->p.precision, [&](auto t, auto) {
+        return lbm::launch_conserved<decltype(t)>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(),
+                                                  h->stream);
+    });
     double tmp[2] = {0.0, 0.0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->sums(), 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_conserved", e);

@@ -2,9 +2,13 @@
 // the kernel launchers that the C ABI (lbm_api.cu) dispatches to.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+
+#include "lbm.h"
 
 namespace lbm {
 
@@ -58,8 +62,22 @@ struct Coeffs {
 
 inline size_t lattice_elems(const Geometry& g, int nq) { return (size_t)g.ny * g.nxb * nq * 32; }
 
-// Launchers (one instantiation per precision, defined in lbm_step_f32.cu /
-// lbm_step_f64.cu).  `src` holds the post-collision populations of the last
+// Storage precisions: the type T a population is stored in and the type R the
+// collision computes in.  by_storage calls fn(T{}, R{}) for a precision code.
+//   LBM_FP64 -> (double, double)         LBM_FP32 -> (float, float)
+//   LBM_FP32_BF16STORE -> (bf16, float)  LBM_FP32_FP16STORE -> (half, float)
+template <typename Fn>
+auto by_storage(int precision, Fn&& fn) {
+    switch (precision) {
+        case LBM_FP64: return fn(double{}, double{});
+        case LBM_FP32_BF16STORE: return fn(__nv_bfloat16{}, float{});
+        case LBM_FP32_FP16STORE: return fn(__half{}, float{});
+        default: return fn(float{}, float{});
+    }
+}
+
+// Launchers (one instantiation per storage type, defined in lbm_step_f64.cu,
+// lbm_step_f32.cu, lbm_step_bf16.cu and lbm_step_f16.cu).  `src` holds the post-collision populations of the last
 // step (pull scheme: streaming happens on the read), `dst` receives the new
 // ones; `prev` holds phi, ux, uy, c1, c2 of the last step (updated in place).
 template <typename T, typename R>

@@ -34,6 +34,11 @@
 
 #include "lbm_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 namespace lbm {
 
 // ---- lattice: D2Q9 order rest, +x, +y, -x, -y, (+,+), (-,+), (-,-), (+,-) ----
@@ -78,6 +83,99 @@ template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 template <typename T>
 __device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
+__device__ __forceinline__ void stcs(__half* p, __half v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
+}
+__device__ __forceinline__ void stcs(__nv_bfloat16* p, __nv_bfloat16 v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+}
+
+// Storage <-> arithmetic conversions (16-bit storage rounds to nearest even).
+template <typename T>
+struct IsHalf { static constexpr bool value = false; };
+template <>
+struct IsHalf<__half> { static constexpr bool value = true; };
+template <>
+struct IsHalf<__nv_bfloat16> { static constexpr bool value = true; };
+template <typename R>
+__device__ __forceinline__ R to_r(int v) { return R(v); }
+template <typename R>
+__device__ __forceinline__ R to_r(float v) { return R(v); }
+template <typename R>
+__device__ __forceinline__ R to_r(double v) { return R(v); }
+template <typename R>
+__device__ __forceinline__ R to_r(__half v) { return R(__half2float(v)); }
+template <typename R>
+__device__ __forceinline__ R to_r(__nv_bfloat16 v) { return R(__bfloat162float(v)); }
+template <typename T, typename R>
+__device__ __forceinline__ T from_r(R v) {
+    if constexpr (std::is_same<T, __half>::value) return __float2half_rn(float(v));
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float2bfloat16_rn(float(v));
+    else return T(v);
+}
+
+// IEEE half storage keeps g_i * 2^10: the flow populations are of the order of
+// the pressure (1e-6 .. 1e-2 in lattice units), much of which lies below half's
+// smallest normal number (6.1e-5), while |g_i| 2^10 stays far below its largest
+// (65504) for any state with |u| < 1.  Scaling by a power of two is exact.
+template <typename T>
+struct GScale { static constexpr float up = 1.0f, down = 1.0f; };
+template <>
+struct GScale<__half> { static constexpr float up = 1024.0f, down = 1.0f / 1024.0f; };
+template <typename T, typename R>
+__device__ __forceinline__ R g_value(R stored) {
+    if constexpr (std::is_same<T, __half>::value) return stored * R(GScale<T>::down);
+    else return stored;
+}
+template <typename T, typename R>
+__device__ __forceinline__ R g_stored(R v) {
+    if constexpr (std::is_same<T, __half>::value) return v * R(GScale<T>::up);
+    else return v;
+}
+
+// Stochastic rounding to 16 bits (Croci & Giles 2020; Connolly, Higham & Mary
+// 2021): a value between two neighbours of the 16-bit grid is rounded up with
+// probability equal to its distance from the lower one, in ulps.  The stored
+// value is then exact on average, and increments smaller than half an ulp -- the
+// slow diffusive and sharpening updates of the populations -- are not rounded
+// away every step as they are under round-to-nearest.  The random bits are a hash
+// (the 32-bit finalizer of MurmurHash3) of the value's bits and a key per node and
+// population, so a run is deterministic and a checkpoint restarts bit-identically.
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+template <typename T>
+__device__ __forceinline__ T round16_stochastic(float v, uint32_t key) {
+    const uint32_t r = mix32(__float_as_uint(v) ^ key);
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        // bfloat16 is the upper half of the float's bits: add 16 random low bits
+        // and truncate (the carry moves into the exponent where it should)
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16));
+    } else {
+        // half: one ulp at |v| is 2^(e - 10), e = max(exponent of v, -14);
+        // add a uniform fraction of it to |v| and truncate towards zero
+        const float a = fabsf(v);
+        const int e = max((int)(__float_as_uint(a) >> 23) - 127, -14);
+        const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
+        return __float2half_rz(copysignf(fmaf(float(r >> 8) * 0x1p-24f, ulp, a), v));
+    }
+}
+// A value of the arithmetic type R as stored in T: 16-bit storage rounds
+// stochastically with the given key, FP32/FP64 storage converts exactly.
+template <typename T, typename R>
+__device__ __forceinline__ T store_value(R v, uint32_t key) {
+    if constexpr (IsHalf<T>::value) return round16_stochastic<T>(float(v), key);
+    else return T(v);
+}
+// key of population plane q of the node with linear index k
+__device__ __forceinline__ uint32_t pop_key(uint32_t node_key, int q) {
+    return node_key + (uint32_t)q * 0x9e3779b9u;
+}
 
 // Node coordinate seen by a stencil: periodic wrap, or the mirror ghost of
 // a half-way wall (the ghost takes the value of the adjacent fluid node).
@@ -100,16 +198,25 @@ __host__ __device__ constexpr int nq_of(int qs) { return 18 + 2 * qs; }
 // (x, y): the post-collision value of the upstream node x - c_i, or -- if that
 // node is behind a wall -- the node's own value in the opposite direction
 // (half-way bounce-back).  Any node; used off the fast path.
+template <int NQ>
+__device__ __forceinline__ long long pull_off(const Geometry& g, int x, int y, int plane0, int i) {
+    int sx = x - cx(i), sy = y - cy(i);
+    const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+    if ((ox && g.wall_x) || (oy && g.wall_y)) return node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32;
+    if (ox) sx = sx < 0 ? sx + g.nx : sx - g.nx;
+    if (oy) sy = sy < 0 ? sy + g.ny : sy - g.ny;
+    return node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
+}
 template <int NQ, typename T, typename R>
 __device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry& g, int x, int y,
                                       int plane0, int i) {
     int sx = x - cx(i), sy = y - cy(i);
     const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
     if ((ox && g.wall_x) || (oy && g.wall_y))
-        return R(ldg(src + node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32));
+        return to_r<R>(ldg(src + node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32));
     if (ox) sx += sx < 0 ? g.nx : -g.nx;
     if (oy) sy += sy < 0 ? g.ny : -g.ny;
-    return R(ldg(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
+    return to_r<R>(ldg(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
 }
 
 // omp = 1 - phi, passed separately so that it keeps full precision near phi = 1
@@ -171,6 +278,20 @@ template <typename T>
 struct PhaseFix { static constexpr bool on = false; using S = T; };
 template <>
 struct PhaseFix<float> { static constexpr bool on = true; using S = int; };
+// 16-bit storage: f is stored as f_i - w_i / 2 (offset from the weights at
+// phi = 1/2) and handled in FP32 once loaded
+template <>
+struct PhaseFix<__half> { static constexpr bool on = false; using S = float; };
+template <>
+struct PhaseFix<__nv_bfloat16> { static constexpr bool on = false; using S = float; };
+
+// f_i at element offset `off` of a population buffer, in its arithmetic form
+template <typename T>
+__device__ __forceinline__ typename PhaseFix<T>::S load_f(const T* __restrict__ src, long long off, int i) {
+    if constexpr (PhaseFix<T>::on) return ldg(reinterpret_cast<const int*>(src) + off);
+    else if constexpr (IsHalf<T>::value) return to_r<float>(ldg(src + off)) + 0.5f * w9<float>(i);
+    else return ldg(src + off);
+}
 constexpr float FIX_ONE = 2147483648.0f;                 // 2^31
 constexpr float FIX_EPS = 4.656612873077392578125e-10f;  // 2^-31
 constexpr double FIX_EPS_D = 4.656612873077392578125e-10;
@@ -186,14 +307,12 @@ struct NodeFH {
 template <int QS, typename T, typename R>
 __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long long nd,
                                              const int (&doff)[9], NodeFH<T, R, QS>& P) {
-    using FS = typename PhaseFix<T>::S;
-    const FS* fsrc = reinterpret_cast<const FS*>(src);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) P.f[i] = ldg(fsrc + nd + doff[i] + i * 32);
+    for (int i = 0; i < 9; ++i) P.f[i] = load_f<T>(src, nd + doff[i] + i * 32, i);
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
-        P.h1[i] = R(ldg(src + nd + doff[i] + (18 + i) * 32));
-        P.h2[i] = R(ldg(src + nd + doff[i] + (18 + QS + i) * 32));
+        P.h1[i] = to_r<R>(ldg(src + nd + doff[i] + (18 + i) * 32));
+        P.h2[i] = to_r<R>(ldg(src + nd + doff[i] + (18 + QS + i) * 32));
     }
 }
 
@@ -201,10 +320,13 @@ template <int QS, typename T, typename R>
 __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geometry& g, int x,
                                             int y, NodeFH<T, R, QS>& P) {
     constexpr int NQ = nq_of(QS);
-    using FS = typename PhaseFix<T>::S;
-    const FS* fsrc = reinterpret_cast<const FS*>(src);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) P.f[i] = pull_any<NQ, FS, FS>(fsrc, g, x, y, 0, i);
+    for (int i = 0; i < 9; ++i) {
+        if constexpr (PhaseFix<T>::on)
+            P.f[i] = pull_any<NQ, int, int>(reinterpret_cast<const int*>(src), g, x, y, 0, i);
+        else
+            P.f[i] = load_f<T>(src, pull_off<NQ>(g, x, y, 0, i), i);
+    }
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
         P.h1[i] = pull_any<NQ, T, R>(src, g, x, y, 18, i);
@@ -303,7 +425,8 @@ __device__ __forceinline__ PhiStencil<T, R> phi_stencil(const typename PhaseFix<
 // phi - sum_{i>0} f*_i, so sum f* = phi exactly.
 template <typename T, typename R>
 __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename PhaseFix<T>::S (&f)[9],
-                                          typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By) {
+                                          typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By,
+                                          uint32_t key) {
     if constexpr (PhaseFix<T>::on) {
         // f*_i - f_i = w_f (w_i phi - f_i) + w_i c_i . B.  In the offset encoding
         // w_i phi - f_i = w_i Phi - F_i (the w_i / 2 offsets cancel); Phi - 9 F_i
@@ -323,16 +446,19 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
         }
         stcs(oi, phis - sum);
     } else {
+        // 16-bit storage keeps f_i - w_i/2; the rest population takes what the
+        // stored moving populations leave of phi
+        const R off = IsHalf<T>::value ? R(0.5) : R(0);
         const R a0 = omega * phi, keep = R(1) - omega;
         R sum = R(0);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-            const T vs = T(keep * R(f[i]) + w9<R>(i) * (a0 + cB));
-            sum += R(vs);
+            const T vs = store_value<T>(keep * R(f[i]) + w9<R>(i) * (a0 + cB) - off * w9<R>(i), pop_key(key, i));
+            sum += to_r<R>(vs) + off * w9<R>(i);
             stcs(o + i * 32, vs);
         }
-        stcs(o, T(phi - sum));
+        stcs(o, store_value<T>(phi - sum - off * w9<R>(0), key));
     }
 }
 
@@ -415,10 +541,10 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
         if (col_in) {
             if (inner) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = R(ldg(src + nd + doff[i] + (9 + i) * 32));
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ldg(src + nd + doff[i] + (9 + i) * 32)));
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = pull_any<NQ, T, R>(src, g, x, y, 9, i);
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(pull_any<NQ, T, R>(src, g, x, y, 9, i));
             }
             if constexpr (!FIELDS) {
                 const R* pp = prev + node_off<5>(g, x, y);
@@ -514,13 +640,15 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                 const R inv_norm = div_r(R(1), norm_r(dphix, dphiy) + R(1e-4));
                 const R nxv = dphix * inv_norm, nyv = dphiy * inv_norm;
                 T* o = dst + nd;
+                // random-bit key of this node (used by 16-bit storage only)
+                const uint32_t key = IsHalf<T>::value ? mix32((uint32_t)y * 0x01000193u + (uint32_t)x) : 0u;
 
                 // ---- e1. f (Eqs. 23-25) ----
                 {
                     const R sharp = C.force_f * C.four_over_W * phi * omp;
                     const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
                     const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
-                    collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By);
+                    collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By, key);
                 }
                 // ---- e2. g (Eqs. 28-31) ----
                 {
@@ -537,7 +665,7 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                         const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
                         R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
                         if (i == 0) v -= R(3) * omega_g * p;
-                        stcs(o + (9 + i) * 32, T(v));
+                        stcs(o + (9 + i) * 32, store_value<T>(g_stored<T>(v), pop_key(key, 9 + i)));
                     }
                 }
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
@@ -565,18 +693,18 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                         const R w = wq<R, QS>(i);
                         const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
                         const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
-                        const T v1 = T(k1 * cur.h1[i] + w * (a1 + c1B));
-                        const T v2 = T(k2 * cur.h2[i] + w * (a2 + c2B));
-                        s1 += R(v1);
-                        s2 += R(v2);
+                        const T v1 = store_value<T>(k1 * cur.h1[i] + w * (a1 + c1B), pop_key(key, 18 + i));
+                        const T v2 = store_value<T>(k2 * cur.h2[i] + w * (a2 + c2B), pop_key(key, 18 + QS + i));
+                        s1 += to_r<R>(v1);
+                        s2 += to_r<R>(v2);
                         stcs(o + (18 + i) * 32, v1);
                         stcs(o + (18 + QS + i) * 32, v2);
                     }
                     // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
                     // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
                     // without c1 they cannot inherit its rounding, and P1 + P2 is kept
-                    stcs(o + 18 * 32, T((P1 + (S1 - Ht)) - s1));
-                    stcs(o + (18 + QS) * 32, T((P2 - (S1 - Ht)) - s2));
+                    stcs(o + 18 * 32, store_value<T>((P1 + (S1 - Ht)) - s1, pop_key(key, 18)));
+                    stcs(o + (18 + QS) * 32, store_value<T>((P2 - (S1 - Ht)) - s2, pop_key(key, 18 + QS)));
                 }
             }
         }
@@ -598,50 +726,35 @@ __global__ void init_kernel(const double* __restrict__ phi_in, const double* __r
     const size_t k = (size_t)y * g.nx + x;
     const double phi = phi_in[k], c1 = c1_in[k], c2 = c2_in[k];
     const double S1 = C.A * mixed_diffusivity(C, phi, 1.0 - phi) * (C.K * c2 * phi - c1 * (1.0 - phi));
-    // location that direction i of node (x, y) is pulled from (pre-streamed layout)
-    auto where = [&](int plane0, int i) -> long long {
-        int sx = x - cx(i), sy = y - cy(i);
-        const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
-        if ((ox && g.wall_x) || (oy && g.wall_y)) return node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32;
-        if (ox) sx += sx < 0 ? g.nx : -g.nx;
-        if (oy) sy += sy < 0 ? g.ny : -g.ny;
-        return node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
-    };
-    auto put_f = [&](auto* fp, int i, auto v) { fp[where(0, i)] = v; };
+    // populations are written pre-streamed: direction i of node (x, y) goes where
+    // the next step pulls it from
     auto put = [&](int plane0, int i, double v) {
-        int sx = x - cx(i), sy = y - cy(i);
-        const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
-        long long at;
-        if ((ox && g.wall_x) || (oy && g.wall_y)) {
-            at = node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32;
-        } else {
-            if (ox) sx += sx < 0 ? g.nx : -g.nx;
-            if (oy) sy += sy < 0 ? g.ny : -g.ny;
-            at = node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
-        }
-        pop[at] = T(v);
+        pop[pull_off<NQ>(g, x, y, plane0, i)] = from_r<T>(v);
     };
-    using FS = typename PhaseFix<T>::S;
-    FS* fpop = reinterpret_cast<FS*>(pop);
-    for (int i = 0; i < 9; ++i) {
-        const double fi = w9<double>(i) * phi;
-        if constexpr (PhaseFix<T>::on) {
-            // the same rest-population rule as the collision: sum_i F_i = round(phi 2^30)
-            (void)fi;
-        } else {
-            put_f(fpop, i, fi);
-        }
-        put(9, i, 0.0);
-    }
+    for (int i = 0; i < 9; ++i) put(9, i, 0.0);
     if constexpr (PhaseFix<T>::on) {
+        // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31)
+        int* fp = reinterpret_cast<int*>(pop);
         const long long Phi = llrint((phi - 0.5) * 2147483648.0);
         long long rest = Phi;
         for (int i = 1; i < 9; ++i) {
             const long long Fi = llrint(w9<double>(i) * (phi - 0.5) * 2147483648.0);
             rest -= Fi;
-            put_f(fpop, i, (int)Fi);
+            fp[pull_off<NQ>(g, x, y, 0, i)] = (int)Fi;
         }
-        put_f(fpop, 0, (int)rest);
+        fp[pull_off<NQ>(g, x, y, 0, 0)] = (int)rest;
+    } else if constexpr (IsHalf<T>::value) {
+        // stored as f_i - w_i / 2; the rest population takes what the rounded
+        // moving ones leave of phi
+        double sum = 0.0;
+        for (int i = 1; i < 9; ++i) {
+            const T v = from_r<T>(w9<double>(i) * (phi - 0.5));
+            sum += double(to_r<float>(v));
+            pop[pull_off<NQ>(g, x, y, 0, i)] = v;
+        }
+        put(0, 0, (phi - 0.5) - sum);
+    } else {
+        for (int i = 0; i < 9; ++i) put(0, i, w9<double>(i) * phi);
     }
     for (int i = 0; i < QS; ++i) {
         put(18, i, wq<double, QS>(i) * (c1 - 0.5 * S1));
@@ -661,8 +774,6 @@ template <typename T, int QS>
 __global__ void __launch_bounds__(RED_THREADS)
     conserved_partials(const T* __restrict__ pop, Geometry g, double* __restrict__ partials) {
     constexpr int NQ = nq_of(QS);
-    using FS = typename PhaseFix<T>::S;
-    const FS* fp = reinterpret_cast<const FS*>(pop);
     // fixed point: sum of the integers Phi (exact); otherwise sum of phi
     long long ai = 0;
     double a = 0.0, b = 0.0;
@@ -672,10 +783,10 @@ __global__ void __launch_bounds__(RED_THREADS)
         const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
         if constexpr (PhaseFix<T>::on) {
             long long s = 0;
-            for (int i = 0; i < 9; ++i) s += pull_any<NQ, FS, FS>(fp, g, x, y, 0, i);
+            for (int i = 0; i < 9; ++i) s += load_f<T>(pop, pull_off<NQ>(g, x, y, 0, i), i);
             ai += s;
         } else {
-            for (int i = 0; i < 9; ++i) a += pull_any<NQ, FS, double>(fp, g, x, y, 0, i);
+            for (int i = 0; i < 9; ++i) a += double(load_f<T>(pop, pull_off<NQ>(g, x, y, 0, i), i));
         }
         double c = 0.0;
         for (int i = 0; i < QS; ++i)

@@ -31,8 +31,6 @@ template <typename T, int QS>
 __global__ void __launch_bounds__(NA_THREADS)
     na_chunk_partials(const T* __restrict__ pop, lbm::Geometry g, double* __restrict__ part) {
     constexpr int NQ = lbm::nq_of(QS);
-    using FS = typename lbm::PhaseFix<T>::S;
-    const FS* fp = reinterpret_cast<const FS*>(pop);
     const long long n = (long long)g.nx * g.ny;
     const long long k0 = blockIdx.x * NA_CHUNK, k1 = min(k0 + NA_CHUNK, n);
     long long ai = 0;
@@ -41,10 +39,10 @@ __global__ void __launch_bounds__(NA_THREADS)
         const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
         if constexpr (lbm::PhaseFix<T>::on) {
             long long s = 0;
-            for (int i = 0; i < 9; ++i) s += lbm::pull_any<NQ, FS, FS>(fp, g, x, y, 0, i);
+            for (int i = 0; i < 9; ++i) s += lbm::load_f<T>(pop, lbm::pull_off<NQ>(g, x, y, 0, i), i);
             ai += s;
         } else {
-            for (int i = 0; i < 9; ++i) a += lbm::pull_any<NQ, FS, double>(fp, g, x, y, 0, i);
+            for (int i = 0; i < 9; ++i) a += double(lbm::load_f<T>(pop, lbm::pull_off<NQ>(g, x, y, 0, i), i));
         }
         for (int i = 0; i < QS; ++i)
             b += lbm::pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
@@ -140,7 +138,7 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     }
     const int qs = params->scalar_q;
     const int nxb = (params->nx + 31) / 32;
-    const size_t elem = params->precision == LBM_FP64 ? 8 : 4;
+    const size_t elem = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
     const size_t pop_bytes = (size_t)params->ny * nxb * lbm::nq_of(qs) * 32 * elem;
     if (state_bytes < pop_bytes) return na_fail(err, err_len, LBM_ERR_ARG, "state smaller than the populations of these parameters");
 
@@ -182,9 +180,9 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     g.wall_y = params->bc_y == LBM_BC_WALL;
     g.strip_h = params->ny;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = params->precision == LBM_FP64
-                        ? na_launch<double>(d_state, g, qs, scratch, (int)nchunks, s)
-                        : na_launch<float>(d_state, g, qs, scratch, (int)nchunks, s);
+    cudaError_t e = lbm::by_storage(params->precision, [&](auto t, auto) {
+        return na_launch<decltype(t)>(d_state, g, qs, scratch, (int)nchunks, s);
+    });
     if (e == cudaSuccess) {
         if (out_on_device) {
             e = cudaMemcpyAsync(out, scratch + 2 * NA_MAX_CHUNKS, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);

@@ -1,0 +1,37 @@
+// Instantiations of the fused step, field, init and reduction kernels for
+// IEEE half storage with float arithmetic.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <>
+cudaError_t launch_step<__half, float>(const void* src, void* dst, void* prev, const Geometry& g,
+                                const Coeffs<float>& C, int q, unsigned* flag, cudaStream_t s) {
+    return launch_step_impl<__half, float>(src, dst, prev, g, C, q, flag, s);
+}
+
+template <>
+cudaError_t launch_fields<__half, float>(const void* src, const Geometry& g, const Coeffs<float>& C, int q,
+                                  uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    return launch_fields_impl<__half, float>(src, g, C, q, mask, out, out_f64, s);
+}
+
+template <>
+cudaError_t launch_init<__half, float>(const double* phi, const double* c1, const double* c2, void* pop,
+                                void* prev, const Geometry& g, const Coeffs<double>& C, int q,
+                                cudaStream_t s) {
+    return launch_init_impl<__half, float>(phi, c1, c2, pop, prev, g, C, q, s);
+}
+
+template <>
+cudaError_t launch_conserved<__half>(const void* pop, const Geometry& g, int q, double* partials,
+                                 double* out, cudaStream_t s) {
+    return launch_conserved_impl<__half>(pop, g, q, partials, out, s);
+}
+
+template <>
+int step_blocks_per_sm<__half, float>(int q) {
+    return step_blocks_per_sm_impl<__half, float>(q);
+}
+
+}  // namespace lbm

@@ -27,8 +27,9 @@ ERROR_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_UNSTABLE_TAU", -3: "
                -4: "LBM_ERR_CUDA", -5: "LBM_ERR_NONFINITE", -6: "LBM_ERR_TIMEOUT"}
 
 LBM_BC_PERIODIC, LBM_BC_WALL = 0, 1
-LBM_FP64, LBM_FP32 = 0, 1
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+LBM_FP64, LBM_FP32, LBM_FP32_BF16STORE, LBM_FP32_FP16STORE = 0, 1, 2, 3
+# storage of the populations; the arithmetic is FP64 for "fp64", else FP32
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16": LBM_FP32_BF16STORE, "fp16": LBM_FP32_FP16STORE}
 LBM_VISC_LINEAR, LBM_VISC_LOG_C, LBM_VISC_EXP_T = 0, 1, 2
 FIELDS = ("phi", "ux", "uy", "p", "c1", "c2", "rho", "mu")
 FIELD_BITS = {name: 1 << i for i, name in enumerate(FIELDS)}
@@ -138,7 +139,8 @@ class Simulation:
     """One solver instance on one GPU.
 
     params    -- plain dict of lattice-unit parameters (see workloads.BASE)
-    precision -- "fp32" or "fp64"
+    precision -- population storage: "fp64", "fp32", or "bf16"/"fp16" (16-bit
+                 storage, FP32 arithmetic)
     device    -- torch device (default: current CUDA device)
     stream    -- torch.cuda.Stream (default: the current stream of the device)
     """

@@ -58,12 +58,22 @@ def test_workspace_size_and_validation(L):
     # two population buffers of 28 FP32 planes, 5 previous-step macro planes, small extras
     base = 2 * 28 * 4 * 1024 * 2048 + 5 * 4 * 1024 * 2048
     assert base <= n < base + 65536
+    # 16-bit population storage: half the population bytes, FP32 macros
+    for prec in ("bf16", "fp16"):
+        p16 = lbm.make_params(dict(nx=1024, ny=2048), prec)
+        n16 = L.lbm_workspace_bytes(ctypes.byref(p16))
+        base16 = 2 * 28 * 2 * 1024 * 2048 + 5 * 4 * 1024 * 2048
+        assert base16 <= n16 < base16 + 65536
     bad = [dict(nx=0, ny=4), dict(nx=4, ny=4, scalar_q=7), dict(nx=4, ny=4, rho1=-1.0),
            dict(nx=4, ny=4, D2=0.0), dict(nx=4, ny=4, M=0.0), dict(nx=4, ny=4, visc_model=5)]
     for b in bad:
         q = lbm.make_params(b, "fp32")
         assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0, b
         assert L.lbm_last_error(None)
+    for code in (-1, 4):  # precision codes outside LBM_FP64 .. LBM_FP32_FP16STORE
+        q = lbm.make_params(dict(nx=4, ny=4), code)
+        assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0
+        assert b"precision" in L.lbm_last_error(None)
 
 
 def test_create_rejects_bad_workspace_without_touching_a_gpu(L):

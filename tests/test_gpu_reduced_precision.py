@@ -1,0 +1,249 @@
+"""16-bit population storage (bfloat16 / IEEE half, FP32 arithmetic) against
+the FP64 oracle, the erfc closed form and the FP32 path, field by field.
+
+Every stored population is rounded stochastically to the 16-bit grid, whose
+spacing is 2u relative (u = 2^-8 for bfloat16, 2^-11 for half), so each step
+adds zero-mean noise of up to 2u relative to every stored value.  f is stored
+as the offset f_i - w_i/2 (|stored f| <= w_i/2) and g, in half, as g_i 2^10.
+The bounds below are about twice the errors measured on these cases (printed
+with -s); they state the accuracy of each storage, field by field.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_15752_gb300 import workloads as wl
+
+from _parity import MAIN_FIELDS, field_scales, rel_max_errors, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+U = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}  # unit roundoff of the stored format
+STORAGES = ("bf16", "fp16")
+
+
+def _report(label, errs):
+    print("\n%-28s " % label + " ".join("%s=%.2e" % (k, v) for k, v in errs.items()))
+
+
+# ------------------------------------------------------------ initial state --
+@pytest.mark.parametrize("storage", STORAGES)
+def test_initial_phase_field_is_within_one_rounding(storage):
+    """Right after init phi is the sum of the stored populations: with the
+    offset encoding only the rest population's rounding reaches phi (the
+    moving ones are summed as stored), so |phi - phi0| <= u w_0 / 2 + FP32 sums."""
+    w = wl.droplet64(nx=70, ny=45, R=12.0)
+    sim = run_gpu(w.params, ("sdf", w.sdf, 1.0, 0.0), 0, storage)
+    got = sim.fields(names=("phi", "c1", "c2"))
+    phi0 = 0.5 + 0.5 * np.tanh(2.0 * w.sdf / w.params["W"])
+    bound = U[storage] * (4.0 / 9.0) / 2.0 + 1e-6
+    assert np.abs(got["phi"] - phi0).max() <= bound
+    # c1 + c2 is the plain sum of 2 x 5 stored h values, each within u of w_i c
+    c_err = np.abs((got["c1"] + got["c2"]) - phi0).max()
+    assert c_err <= 2 * U[storage] + 1e-6
+
+
+# ------------------------------------- planar interface, 1024 x 8, 20000 steps --
+_PLANAR = {}
+
+
+def _planar_oracle():
+    """FP64 oracle of the planar case.  The initial state and the boundaries
+    do not depend on y (periodic in y), so every row of the 1024 x 8 channel
+    evolves like the single row of a 1024 x 1 channel; the oracle runs that."""
+    if "oracle" not in _PLANAR:
+        w = wl.planar1024(ny=1)
+        _PLANAR["oracle"] = run_oracle(w.params, ("sdf", w.sdf, 1.0, 0.0), w.steps).fields()
+    return _PLANAR["oracle"]
+
+
+def _erfc_errors(f, p, steps):
+    """max |c1/phi - exact| on the phase-1 side and |c2/(1-phi) - exact| on the
+    phase-2 side, 3W away from the interface: two semi-infinite phases with a
+    Henry jump c1 = K c2 (Eqs. 8, 9, 12)."""
+    nx = f["phi"].shape[1]
+    x0, D1, D2, K = nx / 2, p["D1"], p["D2"], p["Keq"]
+    r = math.sqrt(D2 / D1)
+    worst = 0.0
+    for row in range(f["phi"].shape[0]):
+        phi, c1, c2 = f["phi"][row], f["c1"][row], f["c2"][row]
+        for i in range(nx):
+            d = i - x0
+            if d < -3 * p["W"]:
+                exact = 1 - r / (K + r) * math.erfc((x0 - i) / (2 * math.sqrt(D1 * steps)))
+                worst = max(worst, abs(c1[i] / phi[i] - exact))
+            elif d > 3 * p["W"]:
+                exact = 1 / (K + r) * math.erfc((i - x0) / (2 * math.sqrt(D2 * steps)))
+                worst = max(worst, abs(c2[i] / (1 - phi[i]) - exact))
+    return worst
+
+
+# Bounds on each field's max error relative to its natural scale: about twice
+# the measured error.  FP32 is here at 20x the step count of the 1e-5 parity
+# cases; its error grows with the steps.
+PLANAR_TOL = {
+    "fp32": dict(phi=1.5e-4, c1=1.5e-4, c2=1.5e-4, rho=1.5e-4, mu=1.5e-4, erfc=3e-3),
+    "bf16": dict(phi=0.25, c1=0.15, c2=0.05, rho=1e-6, mu=1e-6, erfc=0.1),
+    "fp16": dict(phi=0.06, c1=0.025, c2=0.008, rho=1e-6, mu=1e-6, erfc=0.02),
+}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16", "fp16"])
+def test_planar_interface_1024x8_per_storage(storage):
+    w = wl.planar1024()  # 1024 x 8, x walls, D1/D2 = 100, K = 3, 20000 steps
+    want_row = _planar_oracle()
+    want = {k: np.repeat(v, 8, axis=0) for k, v in want_row.items()}
+    sim = run_gpu(w.params, ("sdf", w.sdf, 1.0, 0.0), w.steps, storage)
+    got = sim.fields()
+    errs = rel_max_errors(got, want, MAIN_FIELDS + ("rho", "mu"))
+    e_exact = _erfc_errors(got, w.params, w.steps)
+    e_exact_oracle = _erfc_errors(want_row, w.params, w.steps)
+    flow = {k: float(np.abs(got[k]).max()) for k in ("ux", "uy", "p")}
+    _report("planar1024x8/%s" % storage, dict(errs, erfc=e_exact, erfc_oracle=e_exact_oracle))
+    _report("planar1024x8/%s |flow|" % storage, flow)
+    tol = PLANAR_TOL[storage]
+    for k in ("phi", "c1", "c2", "rho", "mu"):
+        assert errs[k] <= tol[k], (k, errs[k], tol[k])
+    # no flow in the exact solution: what remains is rounding noise of the stored g
+    for k, v in flow.items():
+        assert v <= 1e-3, (k, v)
+    assert e_exact <= tol["erfc"]
+
+
+# ------------------------------------------------ droplet and bubble vs oracle --
+def _droplet():
+    w = wl.droplet64()
+    return w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 1000
+
+
+def _bubble_small():
+    w = wl.bubble1024x2048(nx=96, ny=192)
+    return w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 100
+
+
+CASE_TOL = {  # about twice the measured error, relative to each field's natural scale
+    "droplet64": {
+        "bf16": dict(phi=0.05, ux=1.2, uy=1.2, p=0.4, c1=0.025, c2=0.01, rho=1e-6, mu=1e-6),
+        "fp16": dict(phi=8e-3, ux=0.14, uy=0.14, p=0.06, c1=4e-3, c2=1.6e-3, rho=1e-6, mu=1e-6),
+    },
+    "bubble_small": {
+        "bf16": dict(phi=0.02, ux=1.8, uy=2.7, p=0.06, c1=2.5e-4, c2=0.1, rho=0.02, mu=0.02),
+        "fp16": dict(phi=3.5e-3, ux=0.22, uy=0.26, p=5e-3, c1=2.5e-5, c2=9e-3, rho=3.5e-3,
+                     mu=3.5e-3),
+    },
+}
+_CASE_ORACLE = {}
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("name", ["droplet64", "bubble_small"])
+def test_case_fields_per_storage(name, storage):
+    params, init, steps = {"droplet64": _droplet, "bubble_small": _bubble_small}[name]()
+    if name not in _CASE_ORACLE:
+        _CASE_ORACLE[name] = run_oracle(params, init, steps).fields()
+    want = _CASE_ORACLE[name]
+    got = run_gpu(params, init, steps, storage).fields()
+    errs = rel_max_errors(got, want, MAIN_FIELDS + ("rho", "mu"))
+    _report("%s/%s" % (name, storage), errs)
+    tol = CASE_TOL[name][storage]
+    bad = {k: v for k, v in errs.items() if not v <= tol[k]}
+    assert not bad, (bad, tol)
+
+
+# ------------------------------------------------------------ conservation --
+CONS_TOL = {"bf16": 5e-3, "fp16": 1e-3}
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_conserved_sums_wander_at_rounding_level(storage):
+    """sum phi and sum (c1 + c2) are conserved by the method.  With 16-bit
+    storage the rounding of each stored rest population changes a node's
+    total; stochastic rounding makes that change zero on average, so the
+    totals wander instead of drifting (static droplet, 2000 steps)."""
+    w = wl.droplet64()
+    sim = run_gpu(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 0, storage)
+    s0 = sim.conserved()
+    sim.step(2000)
+    s1 = sim.conserved()
+    rel = np.abs(s1 - s0) / np.abs(s0)
+    _report("conservation/%s" % storage, {"phi": rel[0], "c": rel[1]})
+    assert rel[0] <= CONS_TOL[storage] and rel[1] <= CONS_TOL[storage]
+
+
+# -------------------------------- full-size rising bubble: 16-bit vs FP32 --
+_BUBBLE = {}
+
+
+def _bubble_fp32():
+    w = wl.bubble1024x2048()
+    init = ("sdf", w.sdf, w.c1_tilde, w.c2_tilde)
+    if "fp32" not in _BUBBLE:
+        _BUBBLE["fp32"] = run_gpu(w.params, init, w.steps, "fp32").fields()
+    return w, init, _BUBBLE["fp32"]
+
+
+def _gas_centroid(phi):
+    gas = 1.0 - phi
+    ys, xs = np.mgrid[0:phi.shape[0], 0:phi.shape[1]]
+    a = gas.sum()
+    return a, (gas * xs).sum() / a, (gas * ys).sum() / a
+
+
+def test_bubble_1024x2048_fp16_against_fp32():
+    """The rising bubble at full size (1024 x 2048 walls, density ratio 1000,
+    exp(-beta T) viscosity), 10000 steps: half storage against FP32 storage on
+    the GPU (the FP32 path itself matches the oracle to 1e-5)."""
+    w, init, ref = _bubble_fp32()
+    got = run_gpu(w.params, init, w.steps, "fp16").fields()
+    errs = rel_max_errors(got, ref, MAIN_FIELDS + ("rho", "mu"))
+    sc = field_scales(ref)
+    rms = {k: float(np.sqrt(np.mean((got[k] - ref[k]) ** 2)) / sc[k]) for k in MAIN_FIELDS}
+    _report("bubble1024x2048/fp16 max", errs)
+    _report("bubble1024x2048/fp16 rms", rms)
+    a0, x0, y0 = _gas_centroid(ref["phi"])
+    a1, x1, y1 = _gas_centroid(got["phi"])
+    print("gas centroid fp32 (%.3f, %.3f) area %.1f; fp16 (%.3f, %.3f) area %.1f"
+          % (x0, y0, a0, x1, y1, a1))
+    assert all(np.isfinite(v).all() for v in got.values())
+    # the bubble has risen ~45 nodes; with half storage it trails by a few
+    assert abs(x1 - x0) < 0.5 and abs(y1 - y0) < 5.0
+    assert abs(a1 - a0) / a0 < 0.02
+    assert rms["phi"] < 3e-3 and rms["c1"] < 1e-4 and rms["c2"] < 7e-3
+    assert rms["ux"] < 0.02 and rms["uy"] < 0.08 and rms["p"] < 5e-3
+
+
+def test_bfloat16_storage_of_the_density_ratio_1000_bubble_is_reported_unstable():
+    """bfloat16 keeps 8 significant bits.  In the gas (rho = 1e-3) the velocity
+    is the flow populations' first moment divided by rho, so their rounding
+    noise (2^-8 of g ~ w_i 3p) is amplified a thousandfold and the run blows
+    up; the solver must say so rather than return garbage."""
+    from paper_2402_15752_gb300.lbm import LBM_ERR_NONFINITE, LBMError
+    w = wl.bubble1024x2048(nx=96, ny=192)
+    sim = run_gpu(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 0, "bf16")
+    with pytest.raises(LBMError) as e:
+        for _ in range(20):
+            sim.step(100)
+            sim.sync()
+    assert e.value.code == LBM_ERR_NONFINITE
+
+
+# ------------------------------------------------------------- determinism --
+@pytest.mark.parametrize("storage", STORAGES)
+def test_checkpoint_and_graph_are_bit_identical(storage):
+    w = wl.droplet64(nx=50, ny=41, R=11.0, rho2=0.3, mu2=0.04)
+    init = ("sdf", w.sdf, 1.0, 0.2)
+    a = run_gpu(w.params, init, 0, storage)
+    a.step(40)  # one graph of 32 steps plus 8 single launches
+    b = run_gpu(w.params, init, 0, storage, chunks=[1] * 40)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    st = a.get_state()
+    a.step(17)
+    want = a.fields()
+    a.set_state(st)
+    a.step(17)
+    got = a.fields()
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
