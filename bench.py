@@ -42,7 +42,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bubble1024x2048", choices=["bubble1024x2048", "droplets8192"])
+    ap.add_argument("--workload", default="bubble1024x2048",
+                    choices=["bubble1024x2048", "droplets8192", "batched256"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"],
                     help="population storage (bf16/fp16: 16-bit storage, FP32 arithmetic)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -154,6 +155,11 @@ class ClockSampler:
 
 def make_workload(name, cells_cap=None):
     from paper_2402_15752_gb300 import workloads as wl
+    if name == "batched256":
+        # one case of the batch stands for it on the CPU: the largest that fits
+        cases = wl.batched()
+        fit = [w for w in cases if cells_cap is None or w.cells <= cells_cap]
+        return max(fit or [min(cases, key=lambda w: w.cells)], key=lambda w: w.cells)
     if cells_cap is None:
         return wl.get(name)
     # bounded sample: the same workload with both sides scaled down
@@ -340,11 +346,142 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_batched(args, rank, world, local):
+    """256 independent droplets of uneven sizes in the persistent batched kernel,
+    tile shape picked by the autotuner; compared with stepping every case with its
+    own launches (graph-replayed lbm_step), one case after another."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2402_15752_gb300 import Batch, Simulation
+    from paper_2402_15752_gb300 import workloads as wl
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the GPU path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cases = wl.batched()
+    cells = sum(w.cells for w in cases)
+    sims = [Simulation(w.params, precision="fp32", device=dev) for w in cases]
+    for s, w in zip(sims, cases):
+        s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+    stream = sims[0].stream
+    b = Batch(sims)
+    tune = b.autotune(steps_per_trial=10)
+    b.step(max(3, args.warmup))
+    b.sync()
+
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    sampler = ClockSampler(int(phys) if phys.isdigit() else local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    b.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = whole_job_mlups(world, cells, args.steps, ms)
+
+    # the same cases, each stepped by its own launches, one case after another
+    per_steps = min(args.steps, 500)
+    torch.cuda.synchronize(dev)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for s in sims:
+        s.step(per_steps)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    per_case = cells * per_steps / (p0.elapsed_time(p1) * 1e-3) / 1e6
+
+    bytes_per_cell = 2 * 28 * 4 + 2 * 5 * 4
+    launch_s = ms * 1e-3 / args.steps
+    achieved = bytes_per_cell * cells / launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+
+    e2e = None
+    if not args.no_e2e:
+        sdf_host = [torch.from_numpy(np.ascontiguousarray(w.sdf)).pin_memory() for w in cases]
+        outs = [torch.empty((6, w.params["ny"], w.params["nx"]), dtype=torch.float32).pin_memory()
+                for w in cases]
+        names = ("phi", "ux", "uy", "p", "c1", "c2")
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s, w, h in zip(sims, cases, sdf_host):
+            s.init(h, w.c1_tilde, w.c2_tilde)
+        b.step(args.steps)
+        for s, o in zip(sims, outs):
+            s.fields(names=names, dtype="f32", out=o.numpy())
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ems = max_over_ranks(t0.elapsed_time(t1), world, dev)
+        e2e = {"value": whole_job_mlups(world, cells, args.steps, ems), "unit": "MLUPS",
+               "h2d_bytes_per_step": cells * 8 / args.steps,
+               "d2h_bytes_per_step": 6 * cells * 4 / args.steps}
+        b.sync()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, sw, steps, dt = oracle_mlups(args.workload, 15.0, 64 * 64)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "one %dx%d case of the batch, %d steps, %.1f s, FP64, one thread" % (
+                   sw.params["nx"], sw.params["ny"], steps, dt)}
+
+    if rank == 0:
+        graphs, rest = divmod(args.steps, 32)
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched256", "cases": len(cases), "cells": cells,
+                       "sides": "64..512 step 32", "bc": "periodic", "scalar_q": 5,
+                       "precision": "fp32", "l2": "state larger than L2 (no flush)",
+                       "tiling": {k: tune[k] for k in ("tile_w", "tile_h", "tiles", "ctas")},
+                       "per_case_launches_mlups": per_case, "per_case_steps": per_steps,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_kind, "bytes_per_cell": bytes_per_cell},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": graphs + (1 if rest else 0),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    for s in sims:
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched256":
+        run_batched(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -193,6 +193,76 @@ int lbm_conserved_noalloc(const lbm_params* params, const void* d_state, size_t 
 /* Release the handle (and its CUDA graphs/events); the workspace stays the caller's. */
 void lbm_destroy(lbm_handle* h);
 
+/*
+ * Batched runner.  Many independent lattices of uneven sizes (each an lbm_handle
+ * with its own parameters and workspace) advanced together by one persistent
+ * kernel: each lattice is cut into tiles of tile_w x tile_h nodes, the launch's
+ * CTAs (all co-resident: a cooperative launch) own the tiles round-robin, and a
+ * tile waits only for the tiles of the same lattice whose nodes it reads or that
+ * read its nodes (usually the 8 around it) to finish the previous step (per-tile
+ * step counters), never for the whole grid.  Full runs of
+ * 32 steps are replayed from a captured CUDA graph.  Every node evaluates the
+ * expressions of lbm_step in the same order; the batched kernel is compiled
+ * separately (and once per tile width), so the compiler may fuse a different set
+ * of multiply-adds and results agree with lbm_step to FP32 rounding.  Any two
+ * tile heights of one tile width give identical bits, and runs are deterministic.
+ * The paper runs one case at a time; batching is a service of the library.
+ * Requirements: every case LBM_FP32, one scalar_q, one device and one stream
+ * (the batch runs on it).  The cases stay usable through their own calls
+ * (init, get_fields, conserved, state); if one of them is stepped, initialised or
+ * restored on its own the batch notices and restarts its counters.  Destroy the
+ * batch before its cases.
+ * Waits are bounded: a wait that gives up (spin_limit polls) sets a status bit,
+ * every CTA returns, and lbm_batch_sync reports LBM_ERR_TIMEOUT; the lattices are
+ * then out of step until they are re-initialised and lbm_batch_set_tiling is
+ * called. */
+typedef struct lbm_batch lbm_batch;
+
+/* Bytes of device workspace for the batch's tables (case descriptors, tiles,
+ * neighbour lists, step counters); 0 if the cases do not qualify. */
+size_t lbm_batch_workspace_bytes(lbm_handle* const* cases, int32_t ncases);
+
+/* Build a batch over ncases handles (the array is copied; the handles stay the
+ * caller's) with a caller-owned, 256-byte aligned device workspace.  The initial
+ * tiling is 128 x 16.  Synchronises the stream. */
+int lbm_batch_create(lbm_handle* const* cases, int32_t ncases, void* d_workspace,
+                     size_t workspace_bytes, lbm_batch** out);
+
+/* Tile shape: tile_w in {32, 64, 128} columns, tile_h >= 4 rows.  Rebuilds the
+ * tile tables and restarts the step counters; synchronises. */
+int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_w, int32_t tile_h);
+
+/* Current tile shape, tile count and CTAs per launch (any pointer may be NULL). */
+int lbm_batch_tiling(const lbm_batch* b, int32_t* tile_w, int32_t* tile_h, int32_t* ntiles,
+                     int32_t* grid);
+
+/* Advance every case by nsteps >= 0 time steps (asynchronous on the stream). */
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Synchronise; LBM_ERR_TIMEOUT if a wait gave up, else the first case's
+ * LBM_ERR_NONFINITE, else LBM_OK. */
+int lbm_batch_sync(lbm_batch* b);
+
+/* Time every candidate tiling (tile_w 32, 64, 128 x tile_h 8, 16, 32, 64) over
+ * steps_per_trial steps (after 2 untimed ones) and keep the fastest.  The trial
+ * steps are real steps of every case (every tiling computes the same update), so
+ * the cases advance by 12 * (steps_per_trial + 2) steps.  table (optional) receives
+ * up to table_rows rows of {tile_w, tile_h, ms per step, tiles, CTAs}. */
+int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, double* table, int32_t table_rows,
+                       int32_t* rows_written);
+
+/* Fault injection for tests of the bounded waits: polls per wait before it gives
+ * up (default 2^21, about a second) and a tile whose completion is never
+ * published (-1: none). */
+int lbm_batch_set_wait_limit(lbm_batch* b, int64_t spin_limit, int32_t hold_tile);
+
+/* Release the batch (and its graph); workspace and cases stay the caller's. */
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Message of the batch's last error; with b == NULL, the calling thread's last
+ * lbm_batch_create/lbm_batch_workspace_bytes error. */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Message of the last error on this handle; with h == NULL, the calling thread's
  * last lbm_create/lbm_workspace_bytes error. */
 const char* lbm_last_error(const lbm_handle* h);

@@ -1,0 +1,468 @@
+// C ABI of the batched runner (declared in include/lbm.h): many independent
+// FP32 lattices, each an lbm_handle of its own, advanced together by the
+// persistent batched kernel (lbm_batch_kernels.cuh) in one cooperative launch
+// per call -- or per 32 steps, replayed from a captured CUDA graph -- with the
+// tile shape chosen by timing candidates (lbm_batch_autotune).
+#include "lbm.h"
+#include "lbm_handle.h"
+#include "lbm_internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace {
+
+constexpr size_t BALIGN = 256;
+constexpr int MIN_TILE_H = 4;
+constexpr long long DEFAULT_SPIN_LIMIT = 1LL << 21;  // ~1 s of polling per wait
+thread_local char g_batch_error[512] = "";
+
+size_t balign_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Tiles of the finest tiling any call may choose (32 x MIN_TILE_H): the tables
+// of the workspace are sized for it.
+long long max_tiles(lbm_handle* const* cases, int n) {
+    long long t = 0;
+    for (int i = 0; i < n; ++i)
+        t += (long long)((cases[i]->p.nx + 31) / 32) * ((cases[i]->p.ny + MIN_TILE_H - 1) / MIN_TILE_H);
+    return t;
+}
+
+struct BatchLayout {
+    size_t off_cases, off_tiles, off_nbr, off_done, off_status, total;
+};
+
+BatchLayout batch_layout(int ncases, long long tiles) {
+    BatchLayout L;
+    L.off_cases = 0;
+    L.off_tiles = balign_up(L.off_cases + (size_t)ncases * sizeof(lbm::BatchCase), BALIGN);
+    L.off_nbr = balign_up(L.off_tiles + (size_t)tiles * sizeof(lbm::BatchTile), BALIGN);
+    L.off_done = balign_up(L.off_nbr + (size_t)tiles * lbm::BATCH_NEIGHBOURS * sizeof(int), BALIGN);
+    L.off_status = balign_up(L.off_done + (size_t)tiles * sizeof(unsigned), BALIGN);
+    L.total = L.off_status + BALIGN;
+    return L;
+}
+
+// Checks shared by workspace sizing and creation.
+int check_cases(lbm_handle* const* cases, int n, char* err, size_t len) {
+    if (!cases || n < 1) { snprintf(err, len, "need at least one case"); return LBM_ERR_ARG; }
+    for (int i = 0; i < n; ++i) {
+        const lbm_handle* h = cases[i];
+        if (!h) { snprintf(err, len, "case %d is NULL", i); return LBM_ERR_ARG; }
+        if (h->p.precision != LBM_FP32) { snprintf(err, len, "case %d: the batched runner takes LBM_FP32 lattices", i); return LBM_ERR_ARG; }
+        if (h->p.scalar_q != cases[0]->p.scalar_q) { snprintf(err, len, "case %d: all cases must share scalar_q", i); return LBM_ERR_ARG; }
+        if (h->device != cases[0]->device) { snprintf(err, len, "case %d: all cases must be on one device", i); return LBM_ERR_ARG; }
+        if (h->stream != cases[0]->stream) { snprintf(err, len, "case %d: all cases must share one stream", i); return LBM_ERR_ARG; }
+        for (int j = 0; j < i; ++j)
+            if (cases[j] == h) { snprintf(err, len, "case %d repeats case %d", i, j); return LBM_ERR_ARG; }
+    }
+    return LBM_OK;
+}
+
+using Launch = cudaError_t (*)(const lbm::BatchArgs&, cudaStream_t);
+using Occupancy = int (*)();
+
+bool kernel_for(int q, int tile_w, Launch* launch, Occupancy* occ) {
+#define LBM_PICK(Q, NW)                                 \
+    if (q == Q && tile_w == 32 * NW) {                  \
+        *launch = lbm::launch_batch<Q, NW>;             \
+        *occ = lbm::batch_blocks_per_sm<Q, NW>;         \
+        return true;                                    \
+    }
+    LBM_PICK(5, 1) LBM_PICK(5, 2) LBM_PICK(5, 4)
+    LBM_PICK(9, 1) LBM_PICK(9, 2) LBM_PICK(9, 4)
+#undef LBM_PICK
+    return false;
+}
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<lbm_handle*> cases;
+    int device = 0;
+    int q = 5;
+    cudaStream_t stream = nullptr;
+    uint8_t* ws = nullptr;
+    BatchLayout L{};
+    long long tiles_cap = 0;
+    // current tiling
+    int tile_w = 0, tile_h = 0, ntiles = 0, grid = 0;
+    Launch launch = nullptr;
+    int64_t steps = 0;          // steps since the counters were reset
+    std::vector<int> cur0;      // buffer of each case at the reset
+    long long spin_limit = DEFAULT_SPIN_LIMIT;
+    int hold_tile = -1;
+    bool failed = false;        // a wait gave up: the lattices are out of step
+    cudaGraphExec_t graph = nullptr;
+    bool graph_tried = false;
+    char err[512] = "";
+
+    lbm::BatchCase* d_cases() const { return reinterpret_cast<lbm::BatchCase*>(ws + L.off_cases); }
+    lbm::BatchTile* d_tiles() const { return reinterpret_cast<lbm::BatchTile*>(ws + L.off_tiles); }
+    int* d_nbr() const { return reinterpret_cast<int*>(ws + L.off_nbr); }
+    unsigned* d_done() const { return reinterpret_cast<unsigned*>(ws + L.off_done); }
+    unsigned* d_status() const { return reinterpret_cast<unsigned*>(ws + L.off_status); }
+
+    int fail(int code, const char* what, cudaError_t e = cudaSuccess) {
+        if (e != cudaSuccess) snprintf(err, sizeof(err), "%s: %s", what, cudaGetErrorString(e));
+        else snprintf(err, sizeof(err), "%s", what);
+        return code;
+    }
+
+    void drop_graph() {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        graph_tried = false;
+    }
+
+    lbm::BatchArgs args(int nsteps) const {
+        lbm::BatchArgs a;
+        a.cases = d_cases();
+        a.tiles = d_tiles();
+        a.nbr = d_nbr();
+        a.done = d_done();
+        a.status = d_status();
+        a.ntiles = ntiles;
+        a.nsteps = nsteps;
+        a.spin_limit = spin_limit;
+        a.hold_tile = hold_tile;
+        a.grid = grid;
+        return a;
+    }
+
+    // Case descriptors with each lattice's current buffer, step counters and
+    // status word zeroed (stream-ordered after everything already queued).
+    cudaError_t reset_counters() {
+        std::vector<lbm::BatchCase> hc(cases.size());
+        cur0.resize(cases.size());
+        for (size_t i = 0; i < cases.size(); ++i) {
+            lbm_handle* h = cases[i];
+            lbm::BatchCase& c = hc[i];
+            std::memset(&c, 0, sizeof(c));
+            c.g = h->geo;
+            c.C = h->cf;
+            c.pop[0] = h->pop(0);
+            c.pop[1] = h->pop(1);
+            c.prev = h->prev();
+            c.flag = h->flag();
+            c.cur0 = h->cur;
+            cur0[i] = h->cur;
+        }
+        cudaError_t e = cudaMemcpyAsync(d_cases(), hc.data(), hc.size() * sizeof(lbm::BatchCase),
+                                        cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_done(), 0, (size_t)tiles_cap * sizeof(unsigned), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_status(), 0, BALIGN, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // hc is pageable
+        steps = 0;
+        failed = false;
+        return e;
+    }
+
+    // A case stepped, re-initialised or restored on its own since the last reset
+    // may hold its state in the other buffer: then the counters start over.
+    cudaError_t resync_cases() {
+        for (size_t i = 0; i < cases.size(); ++i)
+            if (cases[i]->cur != ((cur0[i] + (int)(steps & 1)) & 1)) return reset_counters();
+        return cudaSuccess;
+    }
+
+    cudaError_t launch_steps(int n) { return launch(args(n), stream); }
+
+    // A graph of one GRAPH_STEPS-step launch; falls back to plain launches if the
+    // cooperative launch cannot be captured.
+    void try_graph() {
+        graph_tried = true;
+        cudaStream_t cap = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t le = launch(args(lbm::detail::GRAPH_STEPS), cap);
+            e = cudaStreamEndCapture(cap, &g);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess && g) e = cudaGraphInstantiate(&graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) { graph = nullptr; cudaGetLastError(); }
+        cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+// Tiles of every case (row-major per case), their neighbour lists and the launch
+// size for tile_w x tile_h.
+int build_tiling(lbm_batch* b, int tile_w, int tile_h) {
+    Launch launch;
+    Occupancy occ;
+    if (!kernel_for(b->q, tile_w, &launch, &occ)) return b->fail(LBM_ERR_ARG, "tile width must be 32, 64 or 128");
+    if (tile_h < MIN_TILE_H) return b->fail(LBM_ERR_ARG, "tile height must be >= 4");
+    std::vector<lbm::BatchTile> tiles;
+    std::vector<int> nbr;
+    // node coordinate a stencil or pull lands on: periodic wrap or wall clamp
+    auto res = [](int v, int n, bool wall) {
+        if (wall) return std::min(std::max(v, 0), n - 1);
+        v %= n;
+        return v < 0 ? v + n : v;
+    };
+    for (size_t c = 0; c < b->cases.size(); ++c) {
+        const lbm_handle* h = b->cases[c];
+        const int nx = h->p.nx, ny = h->p.ny;
+        const int tx = (nx + tile_w - 1) / tile_w, ty = (ny + tile_h - 1) / tile_h;
+        const int base = (int)tiles.size();
+        const bool wx = h->p.bc_x == LBM_BC_WALL, wy = h->p.bc_y == LBM_BC_WALL;
+        // A tile's step reads the populations of columns x0-2 .. x0+W+1 and rows
+        // ya-2 .. yb+1 (its nodes, its halo ring and their upstream nodes), each
+        // wrapped or clamped.  Tile columns / rows those reads fall in:
+        std::vector<std::vector<int>> col_reach(tx), row_reach(ty);
+        for (int i = 0; i < tx; ++i)
+            for (int xx = i * tile_w - 2; xx <= i * tile_w + tile_w + 1; ++xx) {
+                const int t = res(xx, nx, wx) / tile_w;
+                if (std::find(col_reach[i].begin(), col_reach[i].end(), t) == col_reach[i].end())
+                    col_reach[i].push_back(t);
+            }
+        for (int j = 0; j < ty; ++j)
+            for (int yy = j * tile_h - 2; yy <= std::min(ny, (j + 1) * tile_h) + 1; ++yy) {
+                const int t = res(yy, ny, wy) / tile_h;
+                if (std::find(row_reach[j].begin(), row_reach[j].end(), t) == row_reach[j].end())
+                    row_reach[j].push_back(t);
+            }
+        // A tile waits for every tile it reads (their previous step must be
+        // complete) and for every tile that reads it (they must have finished
+        // reading the buffer it is about to overwrite): the symmetric closure.
+        std::vector<std::vector<int>> wait(tx * ty);
+        for (int j = 0; j < ty; ++j)
+            for (int i = 0; i < tx; ++i) {
+                const int self = j * tx + i;
+                for (int r : row_reach[j])
+                    for (int q : col_reach[i]) {
+                        const int o = r * tx + q;
+                        if (o == self) continue;
+                        wait[self].push_back(o);
+                        wait[o].push_back(self);
+                    }
+            }
+        for (int j = 0; j < ty; ++j)
+            for (int i = 0; i < tx; ++i) {
+                lbm::BatchTile t;
+                t.c = (int)c;
+                t.x0 = i * tile_w;
+                t.ya = j * tile_h;
+                t.yb = std::min(ny, (j + 1) * tile_h);
+                tiles.push_back(t);
+                std::vector<int>& w = wait[j * tx + i];
+                std::sort(w.begin(), w.end());
+                w.erase(std::unique(w.begin(), w.end()), w.end());
+                if ((int)w.size() > lbm::BATCH_NEIGHBOURS)
+                    return b->fail(LBM_ERR_ARG, "tiling too fine for a case: a tile would depend on more than 32 others");
+                for (int k = 0; k < lbm::BATCH_NEIGHBOURS; ++k)
+                    nbr.push_back(k < (int)w.size() ? base + w[k] : -1);
+            }
+    }
+    if ((long long)tiles.size() > b->tiles_cap) return b->fail(LBM_ERR_WORKSPACE, "tile table larger than the workspace");
+    int per_sm = occ();
+    cudaGetLastError();
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms <= 0) sms = 1;
+    if (per_sm <= 0) return b->fail(LBM_ERR_CUDA, "batched kernel does not fit on an SM");
+    cudaError_t e = cudaMemcpyAsync(b->d_tiles(), tiles.data(), tiles.size() * sizeof(lbm::BatchTile),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_nbr(), nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the vectors are pageable
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_set_tiling", e);
+    b->drop_graph();
+    b->tile_w = tile_w;
+    b->tile_h = tile_h;
+    b->ntiles = (int)tiles.size();
+    b->grid = (int)std::min<long long>(b->ntiles, (long long)per_sm * sms);
+    b->launch = launch;
+    e = b->reset_counters();
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_set_tiling", e);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_workspace_bytes(lbm_handle* const* cases, int32_t ncases) {
+    if (check_cases(cases, ncases, g_batch_error, sizeof(g_batch_error)) != LBM_OK) return 0;
+    return batch_layout(ncases, max_tiles(cases, ncases)).total;
+}
+
+int lbm_batch_create(lbm_handle* const* cases, int32_t ncases, void* d_workspace, size_t workspace_bytes,
+                     lbm_batch** out) {
+    if (!out) { snprintf(g_batch_error, sizeof(g_batch_error), "out is NULL"); return LBM_ERR_ARG; }
+    *out = nullptr;
+    int rc = check_cases(cases, ncases, g_batch_error, sizeof(g_batch_error));
+    if (rc != LBM_OK) return rc;
+    const long long cap = max_tiles(cases, ncases);
+    const BatchLayout L = batch_layout(ncases, cap);
+    if (!d_workspace || reinterpret_cast<uintptr_t>(d_workspace) % BALIGN != 0 || workspace_bytes < L.total) {
+        snprintf(g_batch_error, sizeof(g_batch_error),
+                 "workspace must be a %zu-byte aligned device buffer of >= %zu bytes", BALIGN, L.total);
+        return LBM_ERR_WORKSPACE;
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) { snprintf(g_batch_error, sizeof(g_batch_error), "out of host memory"); return LBM_ERR_ARG; }
+    b->cases.assign(cases, cases + ncases);
+    b->device = cases[0]->device;
+    b->q = cases[0]->p.scalar_q;
+    b->stream = cases[0]->stream;
+    b->ws = static_cast<uint8_t*>(d_workspace);
+    b->L = L;
+    b->tiles_cap = cap;
+    lbm::detail::DeviceGuard dg(b->device);
+    rc = build_tiling(b, 128, 16);
+    if (rc != LBM_OK) {
+        snprintf(g_batch_error, sizeof(g_batch_error), "%s", b->err);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_tiling(lbm_batch* b, int32_t tile_w, int32_t tile_h) {
+    if (!b) return LBM_ERR_ARG;
+    lbm::detail::DeviceGuard dg(b->device);
+    return build_tiling(b, tile_w, tile_h);
+}
+
+int lbm_batch_tiling(const lbm_batch* b, int32_t* tile_w, int32_t* tile_h, int32_t* ntiles, int32_t* grid) {
+    if (!b) return LBM_ERR_ARG;
+    if (tile_w) *tile_w = b->tile_w;
+    if (tile_h) *tile_h = b->tile_h;
+    if (ntiles) *ntiles = b->ntiles;
+    if (grid) *grid = b->grid;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b) return LBM_ERR_ARG;
+    if (nsteps < 0) return b->fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (b->failed) return b->fail(LBM_ERR_TIMEOUT, "an earlier batched launch gave up waiting; set the tiling again after re-initialising the cases");
+    if (nsteps == 0) return LBM_OK;
+    lbm::detail::DeviceGuard dg(b->device);
+    cudaError_t e = b->resync_cases();
+    int64_t left = nsteps;
+    const int G = lbm::detail::GRAPH_STEPS;
+    if (e == cudaSuccess && left >= G) {
+        if (!b->graph_tried) b->try_graph();
+        while (e == cudaSuccess && left >= G) {
+            e = b->graph ? cudaGraphLaunch(b->graph, b->stream) : b->launch_steps(G);
+            left -= G;
+        }
+    }
+    while (e == cudaSuccess && left > 0) {
+        const int n = (int)std::min<int64_t>(left, 1 << 20);
+        e = b->launch_steps(n);
+        left -= n;
+    }
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_step", e);
+    b->steps += nsteps;
+    for (lbm_handle* h : b->cases) {
+        h->t += nsteps;
+        h->cur = (h->cur + (int)(nsteps & 1)) & 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+    if (!b) return LBM_ERR_ARG;
+    lbm::detail::DeviceGuard dg(b->device);
+    unsigned st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, b->d_status(), sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_sync", e);
+    if (st != 0u) {
+        b->failed = true;
+        return b->fail(LBM_ERR_TIMEOUT, "a batched launch gave up waiting for a neighbouring tile");
+    }
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+        const int rc = lbm_sync(b->cases[i]);
+        if (rc != LBM_OK) {
+            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, b->cases[i]->err);
+            return rc;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, double* table, int32_t table_rows,
+                       int32_t* rows_written) {
+    if (!b) return LBM_ERR_ARG;
+    if (steps_per_trial < 1) return b->fail(LBM_ERR_ARG, "steps_per_trial must be >= 1");
+    lbm::detail::DeviceGuard dg(b->device);
+    static const int widths[] = {32, 64, 128};
+    static const int heights[] = {8, 16, 32, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return b->fail(LBM_ERR_CUDA, "lbm_batch_autotune: events");
+    }
+    int best_w = b->tile_w, best_h = b->tile_h, rows = 0, rc = LBM_OK;
+    double best = -1.0;
+    for (int w : widths) {
+        for (int hgt : heights) {
+            rc = build_tiling(b, w, hgt);
+            if (rc != LBM_OK) break;
+            rc = lbm_batch_step(b, 2);  // first-touch of the new tables
+            cudaError_t e = rc == LBM_OK ? cudaEventRecord(e0, b->stream) : cudaErrorUnknown;
+            if (e == cudaSuccess) e = b->launch_steps(steps_per_trial);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { rc = rc != LBM_OK ? rc : b->fail(LBM_ERR_CUDA, "lbm_batch_autotune", e); break; }
+            b->steps += steps_per_trial;
+            for (lbm_handle* h : b->cases) {
+                h->t += steps_per_trial;
+                h->cur = (h->cur + (steps_per_trial & 1)) & 1;
+            }
+            rc = lbm_batch_sync(b);
+            if (rc != LBM_OK) break;
+            const double per_step = ms / steps_per_trial;
+            if (table && rows < table_rows) {
+                table[5 * rows + 0] = w;
+                table[5 * rows + 1] = hgt;
+                table[5 * rows + 2] = per_step;
+                table[5 * rows + 3] = b->ntiles;
+                table[5 * rows + 4] = b->grid;
+                ++rows;
+            }
+            if (best < 0.0 || per_step < best) { best = per_step; best_w = w; best_h = hgt; }
+        }
+        if (rc != LBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rows_written) *rows_written = rows;
+    if (rc != LBM_OK) return rc;
+    return build_tiling(b, best_w, best_h);
+}
+
+int lbm_batch_set_wait_limit(lbm_batch* b, int64_t spin_limit, int32_t hold_tile) {
+    if (!b) return LBM_ERR_ARG;
+    if (spin_limit < 1) return b->fail(LBM_ERR_ARG, "spin_limit must be >= 1");
+    if (hold_tile < -1 || hold_tile >= b->ntiles) return b->fail(LBM_ERR_ARG, "hold_tile out of range");
+    b->spin_limit = spin_limit;
+    b->hold_tile = hold_tile;
+    b->drop_graph();
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    lbm::detail::DeviceGuard dg(b->device);
+    b->drop_graph();
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_batch_error; }
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal: the solver handle behind the C ABI's lbm_handle, shared by the
+// single-lattice API (lbm_api.cu) and the batched runner (lbm_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <type_traits>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace detail {
+
+constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity is kept)
+
+struct Layout {
+    int nq;             // populations per node
+    size_t elem, relem; // bytes of a stored population / of a previous-step macro
+    int nxb;            // 32-node blocks per row
+    size_t pop_elems, prev_elems;
+    size_t pop_bytes, prev_bytes, part_bytes, misc_bytes;
+    size_t off_pop[2], off_prev, off_part, off_misc, total;
+};
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int dev) : want(dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard() { if (prev >= 0 && prev != want) cudaSetDevice(prev); }
+};
+
+}  // namespace detail
+}  // namespace lbm
+
+struct lbm_handle {
+    lbm_params p;
+    lbm::detail::Layout L;
+    lbm::Geometry geo;
+    lbm::Coeffs<float> cf;
+    lbm::Coeffs<double> cd;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    uint8_t* ws = nullptr;
+    int cur = 0;
+    int64_t t = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned* h_status = nullptr;
+    cudaEvent_t status_ev = nullptr;
+    bool status_pending = false;
+    bool nonfinite = false;  // sticky until the next init / set_state
+    char err[512] = "";
+
+    void* pop(int k) const { return ws + L.off_pop[k]; }
+    void* prev() const { return ws + L.off_prev; }
+    double* partials() const { return reinterpret_cast<double*>(ws + L.off_part); }
+    unsigned* flag() const { return reinterpret_cast<unsigned*>(ws + L.off_misc); }
+    double* sums() const { return reinterpret_cast<double*>(ws + L.off_misc + 16); }
+
+    int fail(int code, const char* what, cudaError_t e = cudaSuccess) {
+        if (e != cudaSuccess) snprintf(err, sizeof(err), "%s: %s", what, cudaGetErrorString(e));
+        else snprintf(err, sizeof(err), "%s", what);
+        return code;
+    }
+
+    template <typename R>
+    const lbm::Coeffs<R>& coeffs() const {
+        if constexpr (std::is_same<R, double>::value) return cd;
+        else return cf;
+    }
+
+    cudaError_t step_once(int from, cudaStream_t s) {
+        return lbm::by_storage(p.precision, [&](auto t, auto r) {
+            using T = decltype(t);
+            using R = decltype(r);
+            return lbm::launch_step<T, R>(pop(from), pop(from ^ 1), prev(), geo, coeffs<R>(), p.scalar_q, flag(), s);
+        });
+    }
+
+    cudaError_t fields(int from, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+        return lbm::by_storage(p.precision, [&](auto t, auto r) {
+            using T = decltype(t);
+            using R = decltype(r);
+            return lbm::launch_fields<T, R>(pop(from), geo, coeffs<R>(), p.scalar_q, mask, out, out_f64, s);
+        });
+    }
+
+    cudaError_t build_graph(int parity) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        int c = parity;
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < lbm::detail::GRAPH_STEPS && le == cudaSuccess; ++k, c ^= 1) le = step_once(c, capture);
+        e = cudaStreamEndCapture(capture, &g);
+        if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&graph[parity], g, 0);
+        cudaGraphDestroy(g);
+        return e;
+    }
+
+    // Non-blocking look at the status word copied back after the last lbm_step.
+    bool nonfinite_seen() {
+        if (status_pending && cudaEventQuery(status_ev) == cudaSuccess) {
+            status_pending = false;
+            if (*h_status != 0u) nonfinite = true;
+        }
+        return nonfinite;
+    }
+};
+

@@ -111,4 +111,43 @@ cudaError_t launch_conserved(const void* pop, const Geometry& geo, int scalar_q,
 template <typename T, typename R>
 int step_blocks_per_sm(int scalar_q);
 
+// ---- batched runner: many independent FP32 lattices in one persistent launch ----
+// One lattice of a batch, as the persistent kernel sees it.
+struct BatchCase {
+    Geometry g;          // strip_h unused
+    Coeffs<float> C;
+    void* pop[2];        // population buffers
+    void* prev;          // previous-step macros
+    unsigned* flag;      // non-finite flag of the lattice
+    int cur0;            // buffer that held the state when the step counters were reset
+};
+// A tile: columns x0 .. x0+W-1 (clipped to nx) of rows ya .. yb-1 of lattice c.
+struct BatchTile {
+    int c, x0, ya, yb;
+};
+// Tiles a tile waits for before each step (-1 = none): those whose nodes its step
+// reads and those that read its nodes.  Usually the 8 around it; a tail tile one
+// row or column wide lets the reads of its neighbours wrap past it, so the list
+// is computed from the actual reads and may be longer.
+constexpr int BATCH_NEIGHBOURS = 32;
+
+struct BatchArgs {
+    const BatchCase* cases;
+    const BatchTile* tiles;
+    const int* nbr;           // BATCH_NEIGHBOURS per tile
+    unsigned* done;           // steps completed, per tile
+    unsigned* status;         // bit 0: a wait gave up
+    int ntiles;
+    int nsteps;               // steps every tile advances in this launch
+    long long spin_limit;     // polls before a wait gives up
+    int hold_tile;            // fault injection: this tile never reports done (-1: none)
+    int grid;                 // CTAs (all co-resident: cooperative launch)
+};
+
+// Tile widths of the batched kernel: 32 * NW columns, NW in {1, 2, 4}.
+template <int QS, int NW>
+cudaError_t launch_batch(const BatchArgs& a, cudaStream_t s);
+template <int QS, int NW>
+int batch_blocks_per_sm();
+
 }  // namespace lbm

@@ -81,6 +81,15 @@ __device__ __forceinline__ double three_fifths(double s) { return 0.6 * s; }
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+// Population / macro loads of the step: through the read-only path when the
+// buffer is constant for the kernel's lifetime (one step per launch), or cached
+// in L2 only (CG) when other CTAs of the same launch rewrite it between steps
+// (the persistent batched kernel), so that no stale L1 line is read.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
 template <typename T>
 __device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
 __device__ __forceinline__ void stcs(__half* p, __half v) {
@@ -207,16 +216,16 @@ __device__ __forceinline__ long long pull_off(const Geometry& g, int x, int y, i
     if (oy) sy = sy < 0 ? sy + g.ny : sy - g.ny;
     return node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
 }
-template <int NQ, typename T, typename R>
+template <int NQ, typename T, typename R, bool CG = false>
 __device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry& g, int x, int y,
                                       int plane0, int i) {
     int sx = x - cx(i), sy = y - cy(i);
     const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
     if ((ox && g.wall_x) || (oy && g.wall_y))
-        return to_r<R>(ldg(src + node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32));
+        return to_r<R>(ld<CG>(src + node_off<NQ>(g, x, y) + (plane0 + opp(i)) * 32));
     if (ox) sx += sx < 0 ? g.nx : -g.nx;
     if (oy) sy += sy < 0 ? g.ny : -g.ny;
-    return to_r<R>(ldg(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
+    return to_r<R>(ld<CG>(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
 }
 
 // omp = 1 - phi, passed separately so that it keeps full precision near phi = 1
@@ -286,11 +295,11 @@ template <>
 struct PhaseFix<__nv_bfloat16> { static constexpr bool on = false; using S = float; };
 
 // f_i at element offset `off` of a population buffer, in its arithmetic form
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ typename PhaseFix<T>::S load_f(const T* __restrict__ src, long long off, int i) {
-    if constexpr (PhaseFix<T>::on) return ldg(reinterpret_cast<const int*>(src) + off);
-    else if constexpr (IsHalf<T>::value) return to_r<float>(ldg(src + off)) + 0.5f * w9<float>(i);
-    else return ldg(src + off);
+    if constexpr (PhaseFix<T>::on) return ld<CG>(reinterpret_cast<const int*>(src) + off);
+    else if constexpr (IsHalf<T>::value) return to_r<float>(ld<CG>(src + off)) + 0.5f * w9<float>(i);
+    else return ld<CG>(src + off);
 }
 constexpr float FIX_ONE = 2147483648.0f;                 // 2^31
 constexpr float FIX_EPS = 4.656612873077392578125e-10f;  // 2^-31
@@ -304,33 +313,33 @@ struct NodeFH {
 };
 
 // Fast pull: interior node at element offset `nd`, upstream offsets `doff`.
-template <int QS, typename T, typename R>
+template <int QS, typename T, typename R, bool CG = false>
 __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long long nd,
                                              const int (&doff)[9], NodeFH<T, R, QS>& P) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) P.f[i] = load_f<T>(src, nd + doff[i] + i * 32, i);
+    for (int i = 0; i < 9; ++i) P.f[i] = load_f<T, CG>(src, nd + doff[i] + i * 32, i);
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
-        P.h1[i] = to_r<R>(ldg(src + nd + doff[i] + (18 + i) * 32));
-        P.h2[i] = to_r<R>(ldg(src + nd + doff[i] + (18 + QS + i) * 32));
+        P.h1[i] = to_r<R>(ld<CG>(src + nd + doff[i] + (18 + i) * 32));
+        P.h2[i] = to_r<R>(ld<CG>(src + nd + doff[i] + (18 + QS + i) * 32));
     }
 }
 
-template <int QS, typename T, typename R>
+template <int QS, typename T, typename R, bool CG = false>
 __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geometry& g, int x,
                                             int y, NodeFH<T, R, QS>& P) {
     constexpr int NQ = nq_of(QS);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         if constexpr (PhaseFix<T>::on)
-            P.f[i] = pull_any<NQ, int, int>(reinterpret_cast<const int*>(src), g, x, y, 0, i);
+            P.f[i] = pull_any<NQ, int, int, CG>(reinterpret_cast<const int*>(src), g, x, y, 0, i);
         else
-            P.f[i] = load_f<T>(src, pull_off<NQ>(g, x, y, 0, i), i);
+            P.f[i] = load_f<T, CG>(src, pull_off<NQ>(g, x, y, 0, i), i);
     }
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
-        P.h1[i] = pull_any<NQ, T, R>(src, g, x, y, 18, i);
-        P.h2[i] = pull_any<NQ, T, R>(src, g, x, y, 18 + QS, i);
+        P.h1[i] = pull_any<NQ, T, R, CG>(src, g, x, y, 18, i);
+        P.h2[i] = pull_any<NQ, T, R, CG>(src, g, x, y, 18 + QS, i);
     }
 }
 
@@ -462,36 +471,36 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
     }
 }
 
-// The fused step (FIELDS = false) or the macroscopic-field evaluation of the
-// current state (FIELDS = true).
-template <typename T, typename R, int QS, bool FIELDS>
-__global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
-    strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
-                 Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
-                 int out_f64) {
+// One tile of the fused step (FIELDS = false) or of the macroscopic-field
+// evaluation of the current state (FIELDS = true): the W columns x0 .. x0+W-1
+// (one thread each) of rows ya .. yb-1, marched upwards.  CG selects the load
+// path (see ld).  The caller's block has exactly W threads.
+template <typename T, typename R, int QS, bool FIELDS, int W, bool CG>
+__device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restrict__ dst,
+                                           R* __restrict__ prev, const Geometry& g, const Coeffs<R>& C,
+                                           unsigned* __restrict__ flag, uint32_t mask,
+                                           void* __restrict__ out, int out_f64, int x0, int ya,
+                                           int yb) {
     constexpr int NQ = nq_of(QS);
-    constexpr int W2 = STRIP_W + 2;
+    constexpr int W2 = W + 2;
     using PS = typename PhaseFix<T>::S;
     __shared__ PS s_phi[4][W2];
     __shared__ R s_c[4][2][W2];
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int x0 = blockIdx.x * STRIP_W;
     const int x = x0 + tid;
-    const int ya = blockIdx.y * g.strip_h;
-    const int yb = min(ya + g.strip_h, g.ny);
     const bool col_in = x < g.nx;
     const int rx = col_in ? x : resolve(x, g.nx, g.wall_x);
     const bool x_inner = col_in && x >= 1 && x <= g.nx - 2;
-    // Halo columns: lane 0 (tid 0) takes the right one, x0 + 128, and lane 31
-    // (tid 127) the left one, x0 - 1.  Each halo node then sits at the same
+    // Halo columns: lane 0 (tid 0) takes the right one, x0 + W, and lane 31
+    // (tid W - 1) the left one, x0 - 1.  Each halo node then sits at the same
     // position in its 32-node block as the lane's own node, so it reuses the
     // lane's upstream offsets on the fast path.
-    const bool halo = tid == 0 || tid == STRIP_W - 1;
-    const int hraw = tid == 0 ? x0 + STRIP_W : x0 - 1;
+    const bool halo = tid == 0 || tid == W - 1;
+    const int hraw = tid == 0 ? x0 + W : x0 - 1;
     const int hx = resolve(hraw, g.nx, g.wall_x);
     const bool h_inner = hraw == hx && hx >= 1 && hx <= g.nx - 2;
-    const int hcol = tid == 0 ? STRIP_W + 1 : 0;
+    const int hcol = tid == 0 ? W + 1 : 0;
 
     // upstream offsets of an interior node (element units, relative to the node)
     const int row = g.nxb * NQ * 32;
@@ -507,9 +516,9 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
         PS phis;
         R phi, c1, c2;
         if (x_inner && ry >= 1 && ry <= g.ny - 2)
-            pull_fh_fast<QS, T, R>(src, node_off<NQ>(g, x, ry), doff, P);
+            pull_fh_fast<QS, T, R, CG>(src, node_off<NQ>(g, x, ry), doff, P);
         else
-            pull_fh_any<QS, T, R>(src, g, rx, ry, P);
+            pull_fh_any<QS, T, R, CG>(src, g, rx, ry, P);
         zeroth<T, R, QS>(C, P, phis, phi, c1, c2);
         s_phi[yy & 3][tid + 1] = phis;
         s_c[yy & 3][0][tid + 1] = c1;
@@ -519,9 +528,9 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
             PS hs;
             R a, b, c;
             if (h_inner && ry >= 1 && ry <= g.ny - 2)
-                pull_fh_fast<QS, T, R>(src, node_off<NQ>(g, hx, ry), doff, hp);
+                pull_fh_fast<QS, T, R, CG>(src, node_off<NQ>(g, hx, ry), doff, hp);
             else
-                pull_fh_any<QS, T, R>(src, g, hx, ry, hp);
+                pull_fh_any<QS, T, R, CG>(src, g, hx, ry, hp);
             zeroth<T, R, QS>(C, hp, hs, a, b, c);
             s_phi[yy & 3][hcol] = hs;
             s_c[yy & 3][0][hcol] = b;
@@ -541,15 +550,15 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
         if (col_in) {
             if (inner) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ldg(src + nd + doff[i] + (9 + i) * 32)));
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ld<CG>(src + nd + doff[i] + (9 + i) * 32)));
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(pull_any<NQ, T, R>(src, g, x, y, 9, i));
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(pull_any<NQ, T, R, CG>(src, g, x, y, 9, i));
             }
             if constexpr (!FIELDS) {
                 const R* pp = prev + node_off<5>(g, x, y);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) pv[k] = pp[k * 32];
+                for (int k = 0; k < 5; ++k) pv[k] = CG ? __ldcg(pp + k * 32) : pp[k * 32];
             }
         }
         // ---- b. zeroth moments of row y+1 (f, h1, h2 pulled once per node) ----
@@ -710,6 +719,18 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
         }
         cur = nxt;
     }
+}
+
+// One launch = one step (or one field evaluation) of a single lattice: CTA
+// (bx, by) owns columns bx*STRIP_W .. +STRIP_W-1 of rows by*strip_h .. +strip_h-1.
+template <typename T, typename R, int QS, bool FIELDS>
+__global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
+    strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
+                 Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
+                 int out_f64) {
+    const int ya = blockIdx.y * g.strip_h;
+    strip_tile<T, R, QS, FIELDS, STRIP_W, false>(src, dst, prev, g, C, flag, mask, out, out_f64,
+                                                 blockIdx.x * STRIP_W, ya, min(ya + g.strip_h, g.ny));
 }
 
 // Initial state: populations at their (source-shifted) equilibria, written at

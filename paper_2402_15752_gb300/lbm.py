@@ -89,6 +89,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_time": (i64, [vp]),
         "lbm_destroy": (None, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_conserved_noalloc": (ctypes.c_int, [P, dp, sz, vp, dp, i32, ctypes.c_char_p, sz]),
+        "lbm_batch_workspace_bytes": (sz, [ctypes.POINTER(vp), i32]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, vp, sz, ctypes.POINTER(vp)]),
+        "lbm_batch_set_tiling": (ctypes.c_int, [vp, i32, i32]),
+        "lbm_batch_tiling": (ctypes.c_int, [vp] + [ctypes.POINTER(i32)] * 4),
+        "lbm_batch_step": (ctypes.c_int, [vp, i64]),
+        "lbm_batch_sync": (ctypes.c_int, [vp]),
+        "lbm_batch_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double), i32,
+                                              ctypes.POINTER(i32)]),
+        "lbm_batch_set_wait_limit": (ctypes.c_int, [vp, i64, i32]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

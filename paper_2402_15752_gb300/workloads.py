@@ -23,6 +23,10 @@ Workloads (all in lattice units):
   viscosity ratio 100 (mu 0.1 / 1e-3, i.e. nu 0.1 liquid / 1.0 gas), sigma 0.01,
   mu = mu_lin(phi) exp(-beta T) with beta ~ U[0, 2], buoyancy g = 1e-6,
   T = c1 + c2 initialised as 1 - phi (tanh across the interface).
+* ``batched`` -- 256 independent droplets for the batched runner: square
+  periodic grids of side drawn uniformly from {64, 96, ..., 512}, radius
+  U[0.15, 0.35] * side, centre jittered by U[-5, 5] nodes, density ratio
+  U[1, 100], K_eq U[0.5, 5], D1/D2 U[1, 100]; 2000 steps.
 * ``droplets8192`` -- 1 to 4 droplets in an 8192x8192 periodic box, radii
   U[10, 60] * 32, density ratio U[1, 100] (single-case scaling run).
 """
@@ -142,11 +146,31 @@ def droplets8192(nx=8192, ny=8192, steps=1000, **over) -> Workload:
     radii = g.uniform(10.0, 60.0, size=n) * scale
     centres = g.uniform(0.0, 1.0, size=(n, 2)) * np.array([nx, ny])
     ratio = float(g.uniform(1.0, 100.0))
-    p = dict(BASE, nx=nx, ny=ny, sigma=0.01, rho1=ratio * 1e-2, rho2=1e-2,
-             mu1=0.1 * ratio * 1e-2, mu2=1e-3, D1=0.1, D2=0.01, Keq=2.0)
+    p = dict(BASE, nx=nx, ny=ny, sigma=0.01, rho1=1.0, rho2=1.0 / ratio,
+             mu1=0.1, mu2=0.1 / ratio, D1=0.1, D2=0.01, Keq=2.0)
     p.update(over)
     return Workload("droplets8192", p, sdf_droplets(nx, ny, centres, radii), 1.0, 0.0, steps,
                     {"radii": radii.tolist(), "centres": centres.tolist(), "rho_ratio": ratio})
+
+
+def batched(n=256, sides=tuple(range(64, 513, 32)), steps=2000) -> list:
+    """n independent droplet cases of uneven sizes (one Workload each)."""
+    g = rng(WORKLOAD_INDEX["batched"])
+    out = []
+    for k in range(n):
+        side = int(g.choice(sides))
+        R = float(g.uniform(0.15, 0.35)) * side
+        xc, yc = side / 2 + g.uniform(-5.0, 5.0, size=2)
+        ratio = float(g.uniform(1.0, 100.0))
+        K = float(g.uniform(0.5, 5.0))
+        dratio = float(g.uniform(1.0, 100.0))
+        # droplet (phase 1) the heavier phase; kinematic viscosity 0.1 in both
+        p = dict(BASE, nx=side, ny=side, sigma=0.01, rho1=1.0, rho2=1.0 / ratio,
+                 mu1=0.1, mu2=0.1 / ratio, D1=0.1, D2=0.1 / dratio, Keq=K)
+        out.append(Workload("batched[%d]" % k, p, sdf_droplet(side, side, xc, yc, R), 1.0, 0.0,
+                            steps, {"R": R, "centre": (float(xc), float(yc)), "rho_ratio": ratio,
+                                    "Keq": K, "D_ratio": dratio}))
+    return out
 
 
 WORKLOADS = {"droplet64": droplet64, "planar1024": planar1024,
