@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_init.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_double]
         L.orc_init_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc_init_macros.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
         L.orc_get_fields.argtypes = [ctypes.c_void_p, dp]
         L.orc_conserved.argtypes = [ctypes.c_void_p, dp]
@@ -132,6 +133,11 @@ class OracleSim:
     def init_fields(self, phi, c1, c2):
         a, b, c = self._grid(phi), self._grid(c1), self._grid(c2)
         lib().orc_init_fields(self._h, _dptr(a), _dptr(b), _dptr(c))
+
+    def init_macros(self, phi, ux, uy, p, c1, c2):
+        """Restart at the equilibria of the six given fields."""
+        a = [self._grid(v) for v in (phi, ux, uy, p, c1, c2)]
+        lib().orc_init_macros(self._h, *[_dptr(v) for v in a])
 
     def step(self, n: int = 1):
         lib().orc_step(self._h, int(n))

@@ -422,6 +422,39 @@ void orc_init_fields(orc_sim* s, const double* phi, const double* c1, const doub
     }
 }
 
+/* Restart from all six macros: populations at the equilibria of Eqs. (24),
+ * (29)-(30) and (35) evaluated with the given phi, u, p, c1, c2; h shifted by
+ * -/+ w_i dt S_1/2 so that Eq. (37) returns c1, c2 (as in orc_init_fields). */
+void orc_init_macros(orc_sim* s, const double* phi, const double* ux, const double* uy,
+                     const double* pr, const double* c1, const double* c2) {
+    const orc_params* p = &s->p;
+    const int N = s->N, qs = p->scalar_q;
+    const double* ws = scalar_weights(qs);
+    memset(s->h1, 0, 9 * (size_t)N * sizeof(double));
+    memset(s->h2, 0, 9 * (size_t)N * sizeof(double));
+    for (int k = 0; k < N; ++k) {
+        cell_in c;
+        cell_out o;
+        memset(&c, 0, sizeof(c));
+        c.phi = phi[k]; c.ux = ux[k]; c.uy = uy[k]; c.p = pr[k]; c.c1 = c1[k]; c.c2 = c2[k];
+        discrete_functions(p, &c, &o);
+        const double S1 = exchange_source(p, phi[k], c1[k], c2[k]);
+        for (int i = 0; i < 9; ++i) {
+            s->f[i * N + k] = o.feq[i];
+            s->g[i * N + k] = o.geq[i];
+        }
+        for (int i = 0; i < qs; ++i) {
+            s->h1[i * N + k] = o.h1eq[i] - ws[i] * 0.5 * DT * S1;
+            s->h2[i * N + k] = o.h2eq[i] + ws[i] * 0.5 * DT * S1;
+        }
+        s->prev[0 * N + k] = phi[k];
+        s->prev[1 * N + k] = ux[k];
+        s->prev[2 * N + k] = uy[k];
+        s->prev[3 * N + k] = c1[k];
+        s->prev[4 * N + k] = c2[k];
+    }
+}
+
 void orc_init(orc_sim* s, const double* sdf, double c1t, double c2t) {
     const int N = s->N;
     double* phi = malloc((size_t)N * sizeof(double));

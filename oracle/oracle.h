@@ -48,6 +48,10 @@ void     orc_destroy(orc_sim* s);
 void     orc_init(orc_sim* s, const double* sdf, double c1t, double c2t);
 /* General initial macros; u = 0, p = 0. */
 void     orc_init_fields(orc_sim* s, const double* phi, const double* c1, const double* c2);
+/* Restart from all six macros: populations at their equilibria (Eqs. 24, 29-30,
+ * 35) for the given phi, u, p, c1, c2, h shifted by -/+ w_i S_1/2. */
+void     orc_init_macros(orc_sim* s, const double* phi, const double* ux, const double* uy,
+                         const double* p, const double* c1, const double* c2);
 void     orc_step(orc_sim* s, long nsteps);
 /* out: ORC_NFIELDS * nx * ny doubles, field-major. */
 void     orc_get_fields(orc_sim* s, double* out);

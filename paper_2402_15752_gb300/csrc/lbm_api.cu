@@ -201,9 +201,11 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
     return LBM_OK;
 }
 
-static int init_common(lbm_handle* h, const double* phi, const double* c1, const double* c2) {
+static int init_common(lbm_handle* h, const double* phi, const double* c1, const double* c2,
+                       const double* ux = nullptr, const double* uy = nullptr, const double* p = nullptr) {
+    const lbm::InitFields in{phi, ux, uy, p, c1, c2};
     cudaError_t e = lbm::by_storage(h->p.precision, [&](auto t, auto r) {
-        return lbm::launch_init<decltype(t), decltype(r)>(phi, c1, c2, h->pop(0), h->prev(), h->geo, h->cd,
+        return lbm::launch_init<decltype(t), decltype(r)>(in, h->pop(0), h->prev(), h->geo, h->cd,
                                                           h->p.scalar_q, h->stream);
     });
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
@@ -247,6 +249,22 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* c1, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(st + 2 * n, c2, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_init_fields copy", e);
     return init_common(h, st, st + n, st + 2 * n);
+}
+
+int lbm_init_macros(lbm_handle* h, const double* phi, const double* ux, const double* uy, const double* p,
+                    const double* c1, const double* c2, int32_t on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (!phi || !ux || !uy || !p || !c1 || !c2) return h->fail(LBM_ERR_ARG, "all six fields must be non-NULL");
+    DeviceGuard dg(h->device);
+    if (on_device) return init_common(h, phi, c1, c2, ux, uy, p);
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    double* st = static_cast<double*>(h->pop(1));  // 48 B per node: fits every population buffer
+    const double* src[6] = {phi, ux, uy, p, c1, c2};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(st + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_init_macros copy", e);
+    return init_common(h, st, st + 4 * n, st + 5 * n, st + n, st + 2 * n, st + 3 * n);
 }
 
 int lbm_step(lbm_handle* h, int64_t nsteps) {

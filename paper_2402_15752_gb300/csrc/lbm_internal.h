@@ -90,12 +90,17 @@ template <typename T, typename R>
 cudaError_t launch_fields(const void* src, const Geometry& geo, const Coeffs<R>& C, int scalar_q,
                           uint32_t mask, void* out, int out_f64, cudaStream_t s);
 
-// Initial populations from phi, c1, c2 (three dense nx*ny double arrays),
-// written pre-streamed so the first pulled read returns them.
+// Macroscopic fields of an initial state: dense nx*ny double arrays; ux, uy, p
+// may be NULL (zero).
+struct InitFields {
+    const double *phi, *ux, *uy, *p, *c1, *c2;
+};
+
+// Initial populations at the equilibria of the given fields, written
+// pre-streamed so the first pulled read returns them.
 template <typename T, typename R>
-cudaError_t launch_init(const double* phi, const double* c1, const double* c2, void* pop,
-                        void* prev, const Geometry& geo, const Coeffs<double>& C, int scalar_q,
-                        cudaStream_t s);
+cudaError_t launch_init(const InitFields& in, void* pop, void* prev, const Geometry& geo,
+                        const Coeffs<double>& C, int scalar_q, cudaStream_t s);
 
 // phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1t phi, c2 = c2t (1 - phi), into
 // three dense staging arrays (sdf may alias phi).

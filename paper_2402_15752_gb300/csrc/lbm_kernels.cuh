@@ -733,33 +733,44 @@ __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
                                                  blockIdx.x * STRIP_W, ya, min(ya + g.strip_h, g.ny));
 }
 
-// Initial state: populations at their (source-shifted) equilibria, written at
-// the upstream node they will be pulled from, so that the first step's read
-// returns exactly f_i = w_i phi, g_i = 0, h_k,i = w_i (c_k -/+ S/2).
+// Initial state: populations at the (source-shifted) equilibria of the given
+// fields, written at the upstream node they will be pulled from, so that the
+// first step's read returns f_i = f_i^eq (Eq. 24), g_i = g_i^eq (Eqs. 29-30) and
+// h_k,i = h_k,i^eq (Eq. 35) -/+ w_i S/2, so that Eq. (37) gives back c_k.
+// With u = 0, p = 0: f_i = w_i phi, g_i = 0, h_k,i = w_i (c_k -/+ S/2).
 template <typename T, typename R, int QS>
-__global__ void init_kernel(const double* __restrict__ phi_in, const double* __restrict__ c1_in,
-                            const double* __restrict__ c2_in, T* __restrict__ pop,
-                            R* __restrict__ prev, Geometry g, Coeffs<double> C) {
+__global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ prev, Geometry g,
+                            Coeffs<double> C) {
     constexpr int NQ = nq_of(QS);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
     const size_t k = (size_t)y * g.nx + x;
-    const double phi = phi_in[k], c1 = c1_in[k], c2 = c2_in[k];
+    const double phi = in.phi[k], c1 = in.c1[k], c2 = in.c2[k];
+    const double ux = in.ux ? in.ux[k] : 0.0, uy = in.uy ? in.uy[k] : 0.0, p = in.p ? in.p[k] : 0.0;
     const double S1 = C.A * mixed_diffusivity(C, phi, 1.0 - phi) * (C.K * c2 * phi - c1 * (1.0 - phi));
+    const double phic = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
+    const double rho = C.rho2 + C.drho * phic, uu = ux * ux + uy * uy;
     // populations are written pre-streamed: direction i of node (x, y) goes where
     // the next step pulls it from
     auto put = [&](int plane0, int i, double v) {
         pop[pull_off<NQ>(g, x, y, plane0, i)] = from_r<T>(v);
     };
-    for (int i = 0; i < 9; ++i) put(9, i, 0.0);
+    auto cu_of = [&](int i) { return double(cx(i)) * ux + double(cy(i)) * uy; };
+    for (int i = 0; i < 9; ++i) {
+        const double w = w9<double>(i), cu = cu_of(i);
+        const double s = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        double v = (i == 0 ? 3.0 * p * (w - 1.0) : 3.0 * p * w) + rho * s;
+        put(9, i, g_stored<T>(v));
+    }
     if constexpr (PhaseFix<T>::on) {
         // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31)
         int* fp = reinterpret_cast<int*>(pop);
         const long long Phi = llrint((phi - 0.5) * 2147483648.0);
         long long rest = Phi;
         for (int i = 1; i < 9; ++i) {
-            const long long Fi = llrint(w9<double>(i) * (phi - 0.5) * 2147483648.0);
+            const double w = w9<double>(i);
+            const long long Fi = llrint((w * phi * (1.0 + 3.0 * cu_of(i)) - 0.5 * w) * 2147483648.0);
             rest -= Fi;
             fp[pull_off<NQ>(g, x, y, 0, i)] = (int)Fi;
         }
@@ -769,22 +780,24 @@ __global__ void init_kernel(const double* __restrict__ phi_in, const double* __r
         // moving ones leave of phi
         double sum = 0.0;
         for (int i = 1; i < 9; ++i) {
-            const T v = from_r<T>(w9<double>(i) * (phi - 0.5));
+            const double w = w9<double>(i);
+            const T v = from_r<T>(w * phi * (1.0 + 3.0 * cu_of(i)) - 0.5 * w);
             sum += double(to_r<float>(v));
             pop[pull_off<NQ>(g, x, y, 0, i)] = v;
         }
         put(0, 0, (phi - 0.5) - sum);
     } else {
-        for (int i = 0; i < 9; ++i) put(0, i, w9<double>(i) * phi);
+        for (int i = 0; i < 9; ++i) put(0, i, w9<double>(i) * phi * (1.0 + 3.0 * cu_of(i)));
     }
     for (int i = 0; i < QS; ++i) {
-        put(18, i, wq<double, QS>(i) * (c1 - 0.5 * S1));
-        put(18 + QS, i, wq<double, QS>(i) * (c2 + 0.5 * S1));
+        const double w = wq<double, QS>(i), e = 1.0 + 3.0 * cu_of(i);
+        put(18, i, w * (c1 * e - 0.5 * S1));
+        put(18 + QS, i, w * (c2 * e + 0.5 * S1));
     }
     R* pp = prev + node_off<5>(g, x, y);
     pp[0] = R(phi);
-    pp[32] = R(0);
-    pp[64] = R(0);
+    pp[32] = R(ux);
+    pp[64] = R(uy);
     pp[96] = R(c1);
     pp[128] = R(c2);
 }
@@ -897,14 +910,13 @@ cudaError_t launch_fields_impl(const void* src, const Geometry& g, const Coeffs<
 }
 
 template <typename T, typename R>
-cudaError_t launch_init_impl(const double* phi, const double* c1, const double* c2, void* pop,
-                             void* prev, const Geometry& g, const Coeffs<double>& C, int q,
-                             cudaStream_t s) {
+cudaError_t launch_init_impl(const InitFields& in, void* pop, void* prev, const Geometry& g,
+                             const Coeffs<double>& C, int q, cudaStream_t s) {
     dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
     if (q == 5)
-        init_kernel<T, R, 5><<<grid, block, 0, s>>>(phi, c1, c2, (T*)pop, (R*)prev, g, C);
+        init_kernel<T, R, 5><<<grid, block, 0, s>>>(in, (T*)pop, (R*)prev, g, C);
     else
-        init_kernel<T, R, 9><<<grid, block, 0, s>>>(phi, c1, c2, (T*)pop, (R*)prev, g, C);
+        init_kernel<T, R, 9><<<grid, block, 0, s>>>(in, (T*)pop, (R*)prev, g, C);
     return cudaGetLastError();
 }
 

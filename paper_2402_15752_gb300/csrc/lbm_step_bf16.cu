@@ -17,10 +17,9 @@ cudaError_t launch_fields<__nv_bfloat16, float>(const void* src, const Geometry&
 }
 
 template <>
-cudaError_t launch_init<__nv_bfloat16, float>(const double* phi, const double* c1, const double* c2, void* pop,
-                                void* prev, const Geometry& g, const Coeffs<double>& C, int q,
-                                cudaStream_t s) {
-    return launch_init_impl<__nv_bfloat16, float>(phi, c1, c2, pop, prev, g, C, q, s);
+cudaError_t launch_init<__nv_bfloat16, float>(const InitFields& in, void* pop, void* prev, const Geometry& g,
+                                const Coeffs<double>& C, int q, cudaStream_t s) {
+    return launch_init_impl<__nv_bfloat16, float>(in, pop, prev, g, C, q, s);
 }
 
 template <>

@@ -17,10 +17,9 @@ cudaError_t launch_fields<float, float>(const void* src, const Geometry& g, cons
 }
 
 template <>
-cudaError_t launch_init<float, float>(const double* phi, const double* c1, const double* c2, void* pop,
-                                void* prev, const Geometry& g, const Coeffs<double>& C, int q,
-                                cudaStream_t s) {
-    return launch_init_impl<float, float>(phi, c1, c2, pop, prev, g, C, q, s);
+cudaError_t launch_init<float, float>(const InitFields& in, void* pop, void* prev, const Geometry& g,
+                                const Coeffs<double>& C, int q, cudaStream_t s) {
+    return launch_init_impl<float, float>(in, pop, prev, g, C, q, s);
 }
 
 template <>

@@ -17,10 +17,9 @@ cudaError_t launch_fields<double, double>(const void* src, const Geometry& g, co
 }
 
 template <>
-cudaError_t launch_init<double, double>(const double* phi, const double* c1, const double* c2, void* pop,
-                                void* prev, const Geometry& g, const Coeffs<double>& C, int q,
-                                cudaStream_t s) {
-    return launch_init_impl<double, double>(phi, c1, c2, pop, prev, g, C, q, s);
+cudaError_t launch_init<double, double>(const InitFields& in, void* pop, void* prev, const Geometry& g,
+                                const Coeffs<double>& C, int q, cudaStream_t s) {
+    return launch_init_impl<double, double>(in, pop, prev, g, C, q, s);
 }
 
 template <>

@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_create": (ctypes.c_int, [P, vp, sz, vp, ctypes.POINTER(vp)]),
         "lbm_init": (ctypes.c_int, [vp, dp, i32, ctypes.c_double, ctypes.c_double]),
         "lbm_init_fields": (ctypes.c_int, [vp, dp, dp, dp, i32]),
+        "lbm_init_macros": (ctypes.c_int, [vp, dp, dp, dp, dp, dp, dp, i32]),
         "lbm_step": (ctypes.c_int, [vp, i64]),
         "lbm_get_fields": (ctypes.c_int, [vp, ctypes.c_uint32, dp, i32, i32]),
         "lbm_conserved": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
@@ -226,6 +227,14 @@ class Simulation:
             raise ValueError("phi, c1, c2 must all be on the host or all on the device")
         _check(self.L, self._h, self.L.lbm_init_fields(self._h, a[0], b[0], c[0], a[1]))
         self._keep = (a[2], b[2], c[2])
+
+    def init_macros(self, phi, ux, uy, p, c1, c2):
+        """Restart at the equilibria of all six macroscopic fields (host or device)."""
+        a = [self._ptr(v) for v in (phi, ux, uy, p, c1, c2)]
+        if len({v[1] for v in a}) != 1:
+            raise ValueError("the six fields must all be on the host or all on the device")
+        _check(self.L, self._h, self.L.lbm_init_macros(self._h, *[v[0] for v in a], a[0][1]))
+        self._keep = tuple(v[2] for v in a)
 
     def step(self, n: int = 1):
         _check(self.L, self._h, self.L.lbm_step(self._h, int(n)))

@@ -1,0 +1,449 @@
+"""Surrogate network: a residual CNN that advances the macroscopic fields of a
+periodic lattice 16 time steps at a time, trained on trajectories of the
+solver, with the solver as its judge and fallback.  Not in the paper.
+
+* Network: six periodic 3x3 convolutions, 48 channels, ReLU between them,
+  input and output (phi, ux, uy, p, C = c1 + c2) normalised per channel, and
+  a residual connection: state(t + 16) = state(t) + net(state(t)).  BF16
+  weights and activations, FP32 accumulation, FP32 master weights (Adam).
+* Every arithmetic step runs in the library's kernels (include/lbm_nn.h):
+  the convolutions and their gradients on the tensor cores, loss, Adam,
+  packing.  This module allocates memory and sequences the calls.
+* Data: droplet trajectories (1-4 droplets, R ~ U[10, 60], density ratio
+  ~ U[1, 100]) run by the solver's batched runner; snapshots every 16 steps
+  after a warm-up.
+* Judge and fallback: every `judge_every` hops the solver is restarted from
+  the last accepted state (lbm_init_macros, C split at the Henry equilibrium)
+  and run 16 steps; where the network's hop differs from it by more than
+  `tol` (RMS, in units of the channel's spread), the solver's result is kept.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import time
+
+import numpy as np
+
+from .batch import Batch
+from .lbm import LBMError, Simulation, load_library
+from . import workloads as wl
+
+LAYERS = ((16, 48), (48, 48), (48, 48), (48, 48), (48, 48), (48, 16))
+HOP = 16
+USED = 5
+CHANNELS = ("phi", "ux", "uy", "p", "C")
+FIELDS6 = ("phi", "ux", "uy", "p", "c1", "c2")
+RELU, RESIDUAL, MASK = 0, 1, 2
+
+
+def nn_lib():
+    L = load_library()
+    if getattr(L, "_nn_ready", False):
+        return L
+    vp, i32, i64, sz, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_float
+    sig = {
+        "lbm_nn_conv3x3": [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, i32, i32, vp],
+        "lbm_nn_flip_weights": [vp, i32, i32, vp, vp],
+        "lbm_nn_conv3x3_wgrad": [vp, i32, vp, i32, vp, vp, sz, i32, i32, i32, vp],
+        "lbm_nn_bias_grad": [vp, i32, i64, vp, vp, vp],
+        "lbm_nn_mse": [vp, vp, i32, i64, vp, vp, vp, vp],
+        "lbm_nn_adam": [vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp],
+        "lbm_nn_pack": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
+        "lbm_nn_unpack": [vp, i32, i32, i32, vp, vp, vp, vp],
+        "lbm_nn_unpack_macros": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
+        "lbm_nn_state_diff": [vp, vp, i32, i64, vp, vp, vp],
+        "lbm_nn_to_bf16": [vp, i64, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = args
+    L.lbm_nn_wgrad_partial_bytes.restype = sz
+    L.lbm_nn_wgrad_partial_bytes.argtypes = [i32, i32, i32, i32, i32]
+    L._nn_ready = True
+    return L
+
+
+def _ck(rc, what):
+    if rc != 0:
+        raise LBMError(rc, what)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def bf16_bits(a: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns, rounded to nearest even."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def to_device_bf16(a: np.ndarray, device):
+    import torch
+    bits = torch.from_numpy(bf16_bits(a).view(np.int16))
+    return bits.to(device).view(torch.bfloat16)
+
+
+class Net:
+    """Parameters, optimiser state and scratch of the six-layer network."""
+
+    def __init__(self, device, seed: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        g = np.random.default_rng(seed)
+        self.w32, self.b32, self.wb, self.wt = [], [], [], []
+        self.mw, self.vw, self.mb, self.vb, self.gw, self.gb = [], [], [], [], [], []
+        self.mask_w, self.mask_b = [], []
+        for l, (ci, co) in enumerate(LAYERS):
+            ci_r = 5 if l == 0 else ci
+            co_r = 5 if l == 5 else co
+            w = np.zeros((co, 9, ci), np.float32)
+            w[:co_r, :, :ci_r] = g.standard_normal((co_r, 9, ci_r)) * math.sqrt(2.0 / (9 * ci_r))
+            if l == 5:
+                w *= 0.1  # start close to the identity map of the residual network
+            mw = np.zeros((co, 9, ci), np.uint8)
+            mw[:co_r, :, :ci_r] = 1
+            mb = np.zeros(co, np.uint8)
+            mb[:co_r] = 1
+            self._add(w, np.zeros(co, np.float32), mw, mb)
+        self.t = 0
+        self.refresh()
+
+    def _add(self, w, b, mw, mb):
+        t, d = self.torch, self.device
+        self.w32.append(t.from_numpy(w).to(d))
+        self.b32.append(t.from_numpy(b).to(d))
+        self.wb.append(to_device_bf16(w, d))
+        self.wt.append(t.empty((w.shape[2], 9, w.shape[0]), dtype=t.bfloat16, device=d))
+        self.mask_w.append(t.from_numpy(mw).to(d))
+        self.mask_b.append(t.from_numpy(mb).to(d))
+        for lst, shape in ((self.mw, w.shape), (self.vw, w.shape), (self.gw, w.shape),
+                           (self.mb, b.shape), (self.vb, b.shape), (self.gb, b.shape)):
+            lst.append(t.zeros(shape, dtype=t.float32, device=d))
+
+    @property
+    def s(self):
+        return ctypes.c_void_p(self.stream.cuda_stream)
+
+    def refresh(self):
+        """Flipped (adjoint) weights for the backward pass, from the bf16 copies."""
+        L = nn_lib()
+        for l in range(1, 6):
+            ci, co = LAYERS[l]
+            _ck(L.lbm_nn_flip_weights(_p(self.wb[l]), ci, co, _p(self.wt[l]), self.s), "flip")
+
+    # -- save / load (FP32 master weights) --
+    def state_dict(self) -> dict:
+        out = {}
+        for l in range(6):
+            out["w%d" % l] = self.w32[l].cpu().numpy()
+            out["b%d" % l] = self.b32[l].cpu().numpy()
+        return out
+
+    def load_state_dict(self, d: dict):
+        t = self.torch
+        for l in range(6):
+            w = np.asarray(d["w%d" % l], dtype=np.float32)
+            self.w32[l].copy_(t.from_numpy(w))
+            self.b32[l].copy_(t.from_numpy(np.asarray(d["b%d" % l], dtype=np.float32)))
+            self.wb[l].copy_(to_device_bf16(w, self.device))
+        self.refresh()
+
+    # -- passes --
+    def forward(self, x32, x16, out32, acts, B, H, W):
+        """out32 = x32 + net(x); acts: 5 bf16 buffers [B, H, W, 48] (kept for
+        backward) or 2 (ping-pong, inference)."""
+        L = nn_lib()
+        cur = x16
+        for l in range(5):
+            ci, co = LAYERS[l]
+            nxt = acts[l] if len(acts) == 5 else acts[l % 2]
+            _ck(L.lbm_nn_conv3x3(_p(cur), ci, _p(self.wb[l]), _p(self.b32[l]), co, RELU, None, None,
+                                 _p(nxt), B, H, W, self.s), "conv%d" % l)
+            cur = nxt
+        _ck(L.lbm_nn_conv3x3(_p(cur), 48, _p(self.wb[5]), _p(self.b32[5]), 16, RESIDUAL, _p(x32), None,
+                             _p(out32), B, H, W, self.s), "conv5")
+
+    def backward(self, x16, acts, dz16, dbuf, scratch, B, H, W):
+        """Gradients of every weight and bias from dz16 = d loss / d out (bf16, 16 ch)."""
+        L = nn_lib()
+        P = B * H * W
+        wpart, bpart = scratch
+        dz = dz16
+        for l in range(5, -1, -1):
+            ci, co = LAYERS[l]
+            a_l = x16 if l == 0 else acts[l - 1]
+            nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W)
+            _ck(L.lbm_nn_conv3x3_wgrad(_p(a_l), ci, _p(dz), co, _p(self.gw[l]), _p(wpart), nb, B, H, W, self.s),
+                "wgrad%d" % l)
+            _ck(L.lbm_nn_bias_grad(_p(dz), co, P, _p(self.gb[l]), _p(bpart), self.s), "bgrad%d" % l)
+            if l > 0:
+                nxt = dbuf[l % 2]
+                _ck(L.lbm_nn_conv3x3(_p(dz), co, _p(self.wt[l]), None, ci, MASK, None, _p(a_l), _p(nxt),
+                                     B, H, W, self.s), "dgrad%d" % l)
+                dz = nxt
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        L = nn_lib()
+        self.t += 1
+        for l in range(6):
+            _ck(L.lbm_nn_adam(_p(self.w32[l]), _p(self.gw[l]), _p(self.mw[l]), _p(self.vw[l]), _p(self.mask_w[l]),
+                              _p(self.wb[l]), self.w32[l].numel(), lr, beta1, beta2, eps, self.t, self.s), "adam w")
+            _ck(L.lbm_nn_adam(_p(self.b32[l]), _p(self.gb[l]), _p(self.mb[l]), _p(self.vb[l]), _p(self.mask_b[l]),
+                              None, self.b32[l].numel(), lr, beta1, beta2, eps, self.t, self.s), "adam b")
+        self.refresh()
+
+
+class Workspace:
+    """Device buffers for batches of B samples of H x W."""
+
+    def __init__(self, B, H, W, device, train=True):
+        import torch
+        t = torch
+        self.B, self.H, self.W = B, H, W
+        P = B * H * W
+        self.x32 = t.zeros((B, H, W, 16), dtype=t.float32, device=device)
+        self.y32 = t.zeros_like(self.x32)
+        self.t32 = t.zeros_like(self.x32)
+        self.x16 = t.zeros((B, H, W, 16), dtype=t.bfloat16, device=device)
+        self.dz16 = t.zeros((B, H, W, 16), dtype=t.bfloat16, device=device)
+        nacts = 5 if train else 2
+        self.acts = [t.empty((B, H, W, 48), dtype=t.bfloat16, device=device) for _ in range(nacts)]
+        self.dbuf = [t.empty((B, H, W, 48), dtype=t.bfloat16, device=device) for _ in range(2)] if train else None
+        L = nn_lib()
+        wbytes = max(L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W) for ci, co in LAYERS)
+        self.scratch = (t.empty(wbytes // 4 + 1, dtype=t.float32, device=device),
+                        t.empty(1024 * 48, dtype=t.float32, device=device))
+        self.loss_part = t.empty(1024, dtype=t.float64, device=device)
+        self.diff_part = t.empty(640 * B, dtype=t.float32, device=device)
+        self.diff = t.empty(B * 10, dtype=t.float32, device=device)
+        self.P = P
+
+
+def droplet_cases(n, seed, side=256, radius=(10.0, 60.0)):
+    """Seeded droplet cases of the surrogate's data: 1-4 droplets, radius
+    U[10, 60], density ratio U[1, 100] (heavy droplets at density 1), K_eq
+    U[0.5, 5], D1/D2 U[1, 100]; scalar 1 in the droplets."""
+    g = np.random.default_rng(wl.SEED_BASE + 1000 + int(seed))
+    out = []
+    for _ in range(n):
+        k = int(g.integers(1, 5))
+        radii = g.uniform(radius[0], radius[1], size=k)
+        centres = g.uniform(0.0, side, size=(k, 2))
+        ratio = float(g.uniform(1.0, 100.0))
+        p = dict(wl.BASE, nx=side, ny=side, sigma=0.01, rho1=1.0, rho2=1.0 / ratio, mu1=0.1,
+                 mu2=0.1 / ratio, D1=0.1, D2=0.1 / float(g.uniform(1.0, 100.0)),
+                 Keq=float(g.uniform(0.5, 5.0)))
+        out.append(wl.Workload("surrogate", p, wl.sdf_droplets(side, side, centres, radii), 1.0, 0.0,
+                               HOP, {"ratio": ratio}))
+    return out
+
+
+def generate(cases, snapshots, device, warm=64, group=128):
+    """Solver trajectories: fields (phi, ux, uy, p, c1, c2) as float planes,
+    [n, snapshots, 6, H, W], one snapshot every HOP steps after `warm` steps."""
+    import torch
+    H, W = cases[0].params["ny"], cases[0].params["nx"]
+    data = torch.empty((len(cases), snapshots, 6, H, W), dtype=torch.float32, device=device)
+    for g0 in range(0, len(cases), group):
+        part = cases[g0:g0 + group]
+        sims = [Simulation(w.params, precision="fp32", device=device) for w in part]
+        for s, w in zip(sims, part):
+            s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+        b = Batch(sims)
+        b.set_tiling(128, 32)
+        b.step(warm)
+        for k in range(snapshots):
+            if k:
+                b.step(HOP)
+            for j, s in enumerate(sims):
+                s.fields(names=FIELDS6, dtype="f32", device=True, out=data[g0 + j, k])
+        b.sync()
+        b.close()
+        for s in sims:
+            s.close()
+    return data
+
+
+def normalisation(data, samples=64):
+    """Per-channel shift and scale of (phi, ux, uy, p, C) from a sample of
+    snapshots (host statistics)."""
+    n = data.shape[0]
+    idx = np.linspace(0, n - 1, min(n, samples)).astype(int)
+    host = data[idx].cpu().numpy()  # [s, snaps, 6, H, W]
+    ch = [host[:, :, 0], host[:, :, 1], host[:, :, 2], host[:, :, 3], host[:, :, 4] + host[:, :, 5]]
+    shift = np.array([float(c.mean()) for c in ch], dtype=np.float32)
+    scale = np.array([1.0 / max(float(c.std()), 1e-12) for c in ch], dtype=np.float32)
+    return shift, scale
+
+
+class Surrogate:
+    def __init__(self, net: Net, shift, scale):
+        import torch
+        self.net = net
+        self.shift = torch.from_numpy(np.asarray(shift, np.float32)).to(net.device)
+        self.scale = torch.from_numpy(np.asarray(scale, np.float32)).to(net.device)
+
+    def save(self, path):
+        d = self.net.state_dict()
+        d["shift"] = self.shift.cpu().numpy()
+        d["scale"] = self.scale.cpu().numpy()
+        np.savez(path, **d)
+
+    @classmethod
+    def load(cls, path, device, stream=None):
+        d = dict(np.load(path))
+        net = Net(device, stream=stream)
+        net.load_state_dict(d)
+        return cls(net, d["shift"], d["scale"])
+
+    def pack(self, fields6, ws, state32, act16=None):
+        L = nn_lib()
+        _ck(L.lbm_nn_pack(_p(fields6), ws.B, ws.H, ws.W, _p(self.shift), _p(self.scale), _p(state32),
+                          _p(act16), self.net.s), "pack")
+
+    def hop(self, ws):
+        """ws.y32 = one network hop of ws.x32 (bf16 copy in ws.x16)."""
+        self.net.forward(ws.x32, ws.x16, ws.y32, ws.acts, ws.B, ws.H, ws.W)
+
+    def unpack(self, state32, ws, fields5):
+        L = nn_lib()
+        _ck(L.lbm_nn_unpack(_p(state32), ws.B, ws.H, ws.W, _p(self.shift), _p(self.scale), _p(fields5),
+                            self.net.s), "unpack")
+
+
+def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, log=print):
+    """Adam on the MSE of one hop over all consecutive snapshot pairs."""
+    import torch
+    net = sur.net
+    n, S = data.shape[0], data.shape[1]
+    H, W = data.shape[3], data.shape[4]
+    ws = Workspace(batch, H, W, net.device, train=True)
+    L = nn_lib()
+    pairs = np.array([(i, k) for i in range(n) for k in range(S - 1)])
+    g = np.random.default_rng(seed)
+    steps = epochs * (len(pairs) // batch)
+    losses = torch.zeros(max(1, steps), dtype=torch.float64, device=net.device)
+    step = 0
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        order = g.permutation(len(pairs))
+        lr_ep = lr * (0.5 * (1.0 + math.cos(math.pi * ep / max(1, epochs))))
+        for b0 in range(0, len(order) - batch + 1, batch):
+            sel = pairs[order[b0:b0 + batch]]
+            ii = torch.from_numpy(sel[:, 0]).to(net.device)
+            kk = torch.from_numpy(sel[:, 1]).to(net.device)
+            xf = data[ii, kk].contiguous()
+            yf = data[ii, kk + 1].contiguous()
+            sur.pack(xf, ws, ws.x32, ws.x16)
+            sur.pack(yf, ws, ws.t32)
+            net.forward(ws.x32, ws.x16, ws.y32, ws.acts, batch, H, W)
+            _ck(L.lbm_nn_mse(_p(ws.y32), _p(ws.t32), USED, ws.P, _p(ws.dz16), _p(ws.loss_part),
+                             _p(losses[step:step + 1]), net.s), "mse")
+            net.backward(ws.x16, ws.acts, ws.dz16, ws.dbuf, ws.scratch, batch, H, W)
+            net.adam(lr_ep)
+            step += 1
+        if log:
+            lh = losses[:step].cpu().numpy()
+            per = max(1, len(order) // batch)
+            log("epoch %d: loss %.4e (first %.4e)  %.1f s" % (ep, lh[-per:].mean(), lh[0], time.perf_counter() - t0))
+    return losses[:step].cpu().numpy()
+
+
+def field_errors(got5, want5):
+    """Per channel: max |got - want| / max |want| (phi, C) or / max speed (u) or
+    / max |p|, on host arrays [B, 5, H, W]."""
+    got5, want5 = np.asarray(got5, np.float64), np.asarray(want5, np.float64)
+    speed = float(np.sqrt(want5[:, 1] ** 2 + want5[:, 2] ** 2).max())
+    scales = [float(np.abs(want5[:, 0]).max()), speed, speed, float(np.abs(want5[:, 3]).max()),
+              float(np.abs(want5[:, 4]).max())]
+    return {c: float(np.abs(got5[:, k] - want5[:, k]).max() / max(scales[k], 1e-30))
+            for k, c in enumerate(CHANNELS)}
+
+
+def rollout(sur: Surrogate, sims, hops, judge_every=0, tol=0.05, keq=None):
+    """Advance the lattices `sims` (one shape, FP32, stepped by one Batch) by
+    `hops` network hops.  With judge_every = m > 0 the solver checks every m-th
+    hop: it restarts from the state the hop started from, runs 16 steps, and its
+    result replaces the network's where their RMS distance (in units of the
+    channel spread) exceeds `tol`.  Returns (fields [B, 5, H, W] on the device,
+    stats)."""
+    import torch
+    net = sur.net
+    B = len(sims)
+    H, W = sims[0].ny, sims[0].nx
+    ws = Workspace(B, H, W, net.device, train=False)
+    L = nn_lib()
+    f6 = torch.empty((B, 6, H, W), dtype=torch.float32, device=net.device)
+    for j, s in enumerate(sims):
+        s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
+    sur.pack(f6, ws, ws.x32, ws.x16)
+    keq_t = torch.tensor([float(s.params["Keq"]) if keq is None else keq[j] for j, s in enumerate(sims)],
+                         dtype=torch.float32, device=net.device)
+    macros = torch.empty((B, 6, H, W), dtype=torch.float64, device=net.device) if judge_every else None
+    lb32 = torch.empty_like(ws.x32) if judge_every else None
+    batch = Batch(sims) if judge_every else None
+    judged = fallbacks = 0
+    for k in range(1, hops + 1):
+        sur.hop(ws)
+        if judge_every and k % judge_every == 0:
+            _ck(L.lbm_nn_unpack_macros(_p(ws.x32), B, H, W, _p(sur.shift), _p(sur.scale), _p(keq_t), _p(macros),
+                                       net.s), "unpack_macros")
+            for j, s in enumerate(sims):
+                m = macros[j]
+                s.init_macros(m[0], m[1], m[2], m[3], m[4], m[5])
+            batch.step(HOP)
+            for j, s in enumerate(sims):
+                s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
+            sur.pack(f6, ws, lb32)
+            _ck(L.lbm_nn_state_diff(_p(ws.y32), _p(lb32), B, H * W, _p(ws.diff_part), _p(ws.diff), net.s), "diff")
+            d = ws.diff.view(B, 5, 2).cpu().numpy()
+            judged += B
+            for j in range(B):
+                if float(d[j, :, 1].max()) > tol:
+                    ws.y32[j].copy_(lb32[j])
+                    fallbacks += 1
+        ws.x32, ws.y32 = ws.y32, ws.x32
+        _ck(L.lbm_nn_to_bf16(_p(ws.x32), ws.x32.numel(), _p(ws.x16), net.s), "to_bf16")
+    if batch is not None:
+        batch.close()
+    out5 = torch.empty((B, 5, H, W), dtype=torch.float32, device=net.device)
+    sur.unpack(ws.x32, ws, out5)
+    return out5, {"judged": judged, "fallbacks": fallbacks}
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser(description="train or evaluate the surrogate network")
+    ap.add_argument("command", choices=["train"])
+    ap.add_argument("--trajectories", type=int, default=2000)
+    ap.add_argument("--snapshots", type=int, default=5)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--side", type=int, default=256)
+    ap.add_argument("--out", default="surrogate.npz")
+    args = ap.parse_args()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    data = generate(droplet_cases(args.trajectories, 0, args.side), args.snapshots, dev)
+    torch.cuda.synchronize()
+    print("data: %d trajectories x %d snapshots in %.1f s" % (args.trajectories, args.snapshots,
+                                                             time.perf_counter() - t0), flush=True)
+    shift, scale = normalisation(data)
+    sur = Surrogate(Net(dev, seed=0), shift, scale)
+    losses = train(sur, data, epochs=args.epochs, batch=args.batch, lr=args.lr)
+    sur.save(args.out)
+    print(json.dumps({"trajectories": args.trajectories, "epochs": args.epochs, "first_loss": float(losses[0]),
+                      "last_loss": float(losses[-100:].mean()), "seconds": time.perf_counter() - t0}))
+
+
+if __name__ == "__main__":
+    main()

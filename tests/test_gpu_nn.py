@@ -1,0 +1,267 @@
+"""The surrogate network's CUDA kernels (lbm_nn_*) against the FP64 reference
+(oracle/conv_ref.py), and the network's training and judged rollout.
+
+Inputs and weights are drawn, rounded to bfloat16 on the host, and handed to
+both sides, so the reference sees exactly the operands the tensor cores do;
+what remains is FP32 accumulation (relative ~1e-6 of the sum of |terms|) and,
+for bfloat16 outputs, one final rounding (2^-8 relative).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import conv_ref as cr
+from paper_2402_15752_gb300 import surrogate as sg
+from paper_2402_15752_gb300.lbm import LBMError
+
+pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -8
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _bf16(a):
+    """Host array -> (device bf16 tensor, float64 copy of the rounded values)."""
+    t = _torch()
+    x = t.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(t.bfloat16)
+    return x.cuda(), x.float().numpy().astype(np.float64)
+
+
+def _f32(a):
+    t = _torch()
+    return t.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _host(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _sync():
+    _torch().cuda.synchronize()
+
+
+@pytest.mark.parametrize("ci,co,epi", [(16, 48, sg.RELU), (48, 48, sg.RELU), (48, 16, sg.RESIDUAL),
+                                       (48, 48, sg.MASK), (16, 48, sg.MASK)])
+def test_conv3x3_matches_the_fp64_reference(ci, co, epi):
+    t = _torch()
+    L = sg.nn_lib()
+    g = np.random.default_rng(ci * 100 + co + epi)
+    B, H, W = 2, 16, 32
+    x, xr = _bf16(g.standard_normal((B, H, W, ci)))
+    w, wr = _bf16(g.standard_normal((co, 9, ci)) / np.sqrt(9 * ci))
+    b = g.standard_normal(co).astype(np.float32)
+    ref = cr.conv3x3(xr, wr, None if epi == sg.MASK else b)
+    bound = cr.conv3x3(np.abs(xr), np.abs(wr)) + np.abs(b)  # sum of |terms|
+    res = mask = None
+    if epi == sg.RESIDUAL:
+        r = g.standard_normal((B, H, W, co)).astype(np.float32)
+        res = _f32(r)
+        ref = ref + r
+        y = t.empty((B, H, W, co), dtype=t.float32, device="cuda")
+    else:
+        y = t.empty((B, H, W, co), dtype=t.bfloat16, device="cuda")
+        if epi == sg.RELU:
+            ref = np.maximum(ref, 0.0)
+        else:
+            mask, mr = _bf16(np.maximum(g.standard_normal((B, H, W, co)), 0.0))
+            ref = ref * (mr > 0)
+    rc = L.lbm_nn_conv3x3(_p(x), ci, _p(w), _p(_f32(b)), co, epi, _p(res), _p(mask), _p(y), B, H, W, _stream())
+    assert rc == 0
+    got = _host(y)
+    tol = 1e-5 * bound + (0.0 if epi == sg.RESIDUAL else U_BF16 * np.abs(ref)) + 1e-30
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+
+
+def test_conv3x3_rejects_unsupported_shapes():
+    t = _torch()
+    L = sg.nn_lib()
+    x = t.zeros((1, 12, 32, 48), dtype=t.bfloat16, device="cuda")
+    w = t.zeros((48, 9, 48), dtype=t.bfloat16, device="cuda")
+    y = t.zeros_like(x)
+    assert L.lbm_nn_conv3x3(_p(x), 48, _p(w), None, 48, sg.RELU, None, None, _p(y), 1, 12, 32, None) == -1
+    assert L.lbm_nn_conv3x3(_p(x), 32, _p(w), None, 48, sg.RELU, None, None, _p(y), 1, 16, 32, None) == -1
+
+
+@pytest.mark.parametrize("ci,co", [(16, 48), (48, 48), (48, 16)])
+def test_weight_and_bias_gradients_match_the_reference(ci, co):
+    t = _torch()
+    L = sg.nn_lib()
+    g = np.random.default_rng(ci + 7 * co)
+    B, H, W = 2, 16, 48
+    x, xr = _bf16(g.standard_normal((B, H, W, ci)))
+    dy, dyr = _bf16(g.standard_normal((B, H, W, co)))
+    nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W)
+    part = t.empty(nb // 4 + 1, dtype=t.float32, device="cuda")
+    dw = t.empty((co, 9, ci), dtype=t.float32, device="cuda")
+    assert L.lbm_nn_conv3x3_wgrad(_p(x), ci, _p(dy), co, _p(dw), _p(part), nb, B, H, W, _stream()) == 0
+    ref = cr.conv3x3_wgrad(xr, dyr)
+    bound = cr.conv3x3_wgrad(np.abs(xr), np.abs(dyr))
+    assert np.all(np.abs(_host(dw) - ref) <= 1e-5 * bound + 1e-30)
+    db = t.empty(co, dtype=t.float32, device="cuda")
+    bpart = t.empty(1024 * co, dtype=t.float32, device="cuda")
+    assert L.lbm_nn_bias_grad(_p(dy), co, B * H * W, _p(db), _p(bpart), _stream()) == 0
+    np.testing.assert_allclose(_host(db), dyr.sum(axis=(0, 1, 2)), rtol=0, atol=1e-5 * np.abs(dyr).sum())
+
+
+def test_adjoint_convolution_through_flipped_weights():
+    """dgrad = conv of dy with the flipped weights (LBM_NN_MASK with an all-ones mask)."""
+    t = _torch()
+    L = sg.nn_lib()
+    g = np.random.default_rng(3)
+    B, H, W = 1, 8, 16
+    w, wr = _bf16(g.standard_normal((48, 9, 48)) / 20)
+    dy, dyr = _bf16(g.standard_normal((B, H, W, 48)))
+    wt = t.empty((48, 9, 48), dtype=t.bfloat16, device="cuda")
+    assert L.lbm_nn_flip_weights(_p(w), 48, 48, _p(wt), _stream()) == 0
+    ones = t.ones((B, H, W, 48), dtype=t.bfloat16, device="cuda")
+    dx = t.empty((B, H, W, 48), dtype=t.bfloat16, device="cuda")
+    assert L.lbm_nn_conv3x3(_p(dy), 48, _p(wt), None, 48, sg.MASK, None, _p(ones), _p(dx), B, H, W, _stream()) == 0
+    ref = cr.conv3x3_dgrad(dyr, wr)
+    bound = cr.conv3x3_dgrad(np.abs(dyr), np.abs(wr))
+    assert np.all(np.abs(_host(dx) - ref) <= 1e-5 * bound + U_BF16 * np.abs(ref))
+
+
+def test_mse_and_adam_match_the_reference():
+    t = _torch()
+    L = sg.nn_lib()
+    g = np.random.default_rng(4)
+    P = 8 * 64
+    pred = g.standard_normal((P, 16)).astype(np.float32)
+    targ = g.standard_normal((P, 16)).astype(np.float32)
+    dz = t.empty((P, 16), dtype=t.bfloat16, device="cuda")
+    part = t.empty(1024, dtype=t.float64, device="cuda")
+    loss = t.zeros(1, dtype=t.float64, device="cuda")
+    assert L.lbm_nn_mse(_p(_f32(pred)), _p(_f32(targ)), 5, P, _p(dz), _p(part), _p(loss), _stream()) == 0
+    d = pred[:, :5].astype(np.float64) - targ[:, :5]
+    assert float(loss.item()) == pytest.approx(float((d ** 2).mean()), rel=1e-12)
+    want = np.zeros((P, 16))
+    want[:, :5] = 2 * d / (P * 5)
+    np.testing.assert_allclose(_host(dz), want, rtol=U_BF16, atol=1e-30)
+    # Adam: three steps against the float64 textbook update
+    n = 1000
+    p0, gr = g.standard_normal(n).astype(np.float32), g.standard_normal(n).astype(np.float32)
+    mask = (g.random(n) > 0.2).astype(np.uint8)
+    pd, gd = _f32(p0), _f32(gr)
+    m, v = t.zeros(n, device="cuda"), t.zeros(n, device="cuda")
+    wb = t.empty(n, dtype=t.bfloat16, device="cuda")
+    pr, mr, vr = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in (1, 2, 3):
+        assert L.lbm_nn_adam(_p(pd), _p(gd), _p(m), _p(v), _p(t.from_numpy(mask).cuda()), _p(wb), n,
+                             1e-2, 0.9, 0.999, 1e-8, step, _stream()) == 0
+        pr, mr, vr = cr.adam(pr, gr.astype(np.float64), mr, vr, step, 1e-2)
+        pr = pr * mask
+    np.testing.assert_allclose(_host(pd), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(_host(wb), pr, rtol=U_BF16, atol=1e-6)
+
+
+def _bf(a):
+    t = _torch()
+    return t.from_numpy(np.asarray(a, dtype=np.float32)).to(t.bfloat16).float().numpy().astype(np.float64)
+
+
+def _grads_with_bf16_storage(x, target, weights, biases):
+    """The reference's backward pass with the GPU's storage points rounded to
+    bfloat16: activations after each ReLU, the loss gradient, and each masked
+    input gradient.  Every other operation is the FP64 reference's."""
+    acts = [x]
+    for l in range(5):
+        acts.append(_bf(np.maximum(cr.conv3x3(acts[-1], weights[l], biases[l]), 0.0)))
+    out = x + cr.conv3x3(acts[5], weights[5], biases[5])
+    npx = out.shape[0] * out.shape[1] * out.shape[2]
+    diff = np.zeros_like(out)
+    diff[..., :5] = out[..., :5] - target[..., :5]
+    dz = _bf(2.0 * diff / (npx * 5))
+    gw, gb = [None] * 6, [None] * 6
+    for l in range(5, -1, -1):
+        gw[l] = cr.conv3x3_wgrad(acts[l], dz)
+        gb[l] = dz.sum(axis=(0, 1, 2))
+        if l > 0:
+            dz = _bf(cr.conv3x3_dgrad(dz, weights[l]) * (acts[l] > 0.0))
+    return gw, gb
+
+
+def test_network_gradients_match_the_fp64_backward():
+    """Full forward and backward of the six-layer network on the GPU against
+    the FP64 reference on the same bfloat16 weights and input.  Against the
+    reference with the GPU's bfloat16 storage points the gradients agree to
+    8e-5 (last layer) .. 1e-2 (first layer) norm-wise, as measured: what is left
+    is FP32 accumulation plus the few ReLU masks and roundings that fall on the
+    other side of a boundary, amplified by cancellation towards the input.  The
+    bound is 2.5e-2; against the plain FP64 reference (no bfloat16 storage
+    between layers, measured 4.5e-4 .. 5.8e-2) it is 1e-1."""
+    t = _torch()
+    B, H, W = 2, 16, 32
+    net = sg.Net("cuda", seed=5)
+    ws = sg.Workspace(B, H, W, "cuda", train=True)
+    g = np.random.default_rng(6)
+    x = np.zeros((B, H, W, 16), np.float32)
+    x[..., :5] = g.standard_normal((B, H, W, 5))
+    x = t.from_numpy(x).to(t.bfloat16).float().numpy()  # the float state equals its bf16 copy
+    target = np.zeros_like(x)
+    target[..., :5] = x[..., :5] + 0.3 * g.standard_normal((B, H, W, 5))
+    ws.x32.copy_(t.from_numpy(x))
+    ws.x16.copy_(t.from_numpy(x).to(t.bfloat16))
+    ws.t32.copy_(t.from_numpy(target))
+    L = sg.nn_lib()
+    loss = t.zeros(1, dtype=t.float64, device="cuda")
+    net.forward(ws.x32, ws.x16, ws.y32, ws.acts, B, H, W)
+    assert L.lbm_nn_mse(_p(ws.y32), _p(ws.t32), 5, ws.P, _p(ws.dz16), _p(ws.loss_part), _p(loss), net.s) == 0
+    net.backward(ws.x16, ws.acts, ws.dz16, ws.dbuf, ws.scratch, B, H, W)
+    _sync()
+    weights = [_host(net.wb[l]) for l in range(6)]
+    biases = [_host(net.b32[l]) for l in range(6)]
+    xr = x.astype(np.float64)
+    lref, gw, gb = cr.net_loss_and_grads(xr, target, weights, biases)
+    assert float(loss.item()) == pytest.approx(lref, rel=2e-2)
+    ew_, eb_ = _grads_with_bf16_storage(xr, target.astype(np.float64), weights, biases)
+    for l in range(6):
+        gw_gpu, gb_gpu = _host(net.gw[l]), _host(net.gb[l])
+        e_store = (np.linalg.norm(gw_gpu - ew_[l]) / np.linalg.norm(ew_[l]),
+                   np.linalg.norm(gb_gpu - eb_[l]) / max(np.linalg.norm(eb_[l]), 1e-30))
+        e_plain = (np.linalg.norm(gw_gpu - gw[l]) / np.linalg.norm(gw[l]),
+                   np.linalg.norm(gb_gpu - gb[l]) / max(np.linalg.norm(gb[l]), 1e-30))
+        print("\nlayer %d: vs bf16-storage reference %.2e %.2e, vs fp64 %.2e %.2e" % ((l,) + e_store + e_plain))
+        assert max(e_store) < 2.5e-2, (l, e_store)
+        assert max(e_plain) < 1e-1, (l, e_plain)
+
+
+def test_training_reduces_the_loss_and_rollout_judge_falls_back():
+    """A few hundred Adam steps on solver trajectories of 64 x 64 droplets cut
+    the one-hop loss; the judged rollout falls back to the solver on every
+    judged hop when the tolerance is zero, and never when it is infinite."""
+    t = _torch()
+    dev = t.device("cuda", 0)
+    cases = sg.droplet_cases(24, seed=1, side=64, radius=(5.0, 12.0))
+    data = sg.generate(cases, snapshots=4, device=dev, warm=32)
+    shift, scale = sg.normalisation(data)
+    sur = sg.Surrogate(sg.Net(dev, seed=2), shift, scale)
+    losses = sg.train(sur, data, epochs=12, batch=8, lr=2e-3, log=None)
+    first, last = float(np.mean(losses[:5])), float(np.mean(losses[-5:]))
+    print("\nloss %.3e -> %.3e over %d steps" % (first, last, len(losses)))
+    assert np.all(np.isfinite(losses)) and last < 0.5 * first
+    # judged rollout on 4 fresh lattices
+    from paper_2402_15752_gb300 import Simulation
+    test_cases = sg.droplet_cases(4, seed=9, side=64, radius=(5.0, 12.0))
+    sims = []
+    for w in test_cases:
+        s = Simulation(w.params, precision="fp32", device=dev)
+        s.init(w.sdf, 1.0, 0.0)
+        s.step(32)
+        sims.append(s)
+    out, st = sg.rollout(sur, sims, hops=4, judge_every=2, tol=0.0)
+    assert st == {"judged": 8, "fallbacks": 8}
+    out2, st2 = sg.rollout(sur, sims, hops=4, judge_every=2, tol=float("inf"))
+    assert st2["fallbacks"] == 0 and bool(t.isfinite(out2).all())

@@ -98,3 +98,29 @@ def test_full_size_bubble_sampled_against_oracle():
     want = run_oracle(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), steps).fields()
     got = run_gpu(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), steps, "fp32").fields()
     assert_parity(got, want, TOL["fp32"], label="bubble1024x2048/fp32")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("steps", [0, 200])
+def test_restart_from_macros_matches_oracle(precision, steps):
+    """lbm_init_macros (populations at the equilibria of given phi, u, p, c1, c2)
+    against the oracle's restart, right after it and 200 steps later."""
+    from _parity import MAIN_FIELDS  # noqa: F401
+    import oracle
+    from paper_2402_15752_gb300 import Simulation
+    w = wl.droplet64(nx=70, ny=45, R=12.0, rho2=0.2, mu2=0.05, wall_y=1)
+    g = np.random.default_rng(7)
+    ny, nx = w.sdf.shape
+    phi = 0.5 + 0.5 * np.tanh(2.0 * w.sdf / w.params["W"])
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    ux = 1e-3 * np.sin(2 * np.pi * xx / nx) * np.cos(np.pi * yy / ny)
+    uy = -1e-3 * np.cos(2 * np.pi * xx / nx) * np.sin(np.pi * yy / ny)
+    p = 1e-4 * g.standard_normal((ny, nx))
+    c1, c2 = 0.8 * phi, 0.3 * (1.0 - phi)
+    o = oracle.OracleSim(w.params)
+    o.init_macros(phi, ux, uy, p, c1, c2)
+    o.step(steps)
+    sim = Simulation(w.params, precision=precision)
+    sim.init_macros(phi, ux, uy, p, c1, c2)
+    sim.step(steps)
+    assert_parity(sim.fields(), o.fields(), TOL[precision], label="restart/%s/%d" % (precision, steps))

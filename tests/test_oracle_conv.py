@@ -1,0 +1,108 @@
+"""Pins of the FP64 network reference (oracle/conv_ref.py) to things other
+than itself: brute-force index loops, a delta kernel that must shift the input,
+the adjoint identities of a linear map, finite differences of the loss through
+the whole residual network, and Adam's closed-form first step."""
+import numpy as np
+import pytest
+
+from oracle import conv_ref as cr
+
+
+def _brute_conv(x, w, b):
+    n, h, wd, ci = x.shape
+    co = w.shape[0]
+    y = np.zeros((n, h, wd, co))
+    for a in range(n):
+        for i in range(h):
+            for j in range(wd):
+                for o in range(co):
+                    s = b[o]
+                    for t in range(9):
+                        dy, dx = t // 3 - 1, t % 3 - 1
+                        for c in range(ci):
+                            s += w[o, t, c] * x[a, (i + dy) % h, (j + dx) % wd, c]
+                    y[a, i, j, o] = s
+    return y
+
+
+def test_conv_matches_brute_force_loops():
+    g = np.random.default_rng(1)
+    x = g.standard_normal((2, 5, 6, 3))
+    w = g.standard_normal((4, 9, 3))
+    b = g.standard_normal(4)
+    np.testing.assert_allclose(cr.conv3x3(x, w, b), _brute_conv(x, w, b), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("t", range(9))
+def test_delta_kernel_shifts_the_input(t):
+    g = np.random.default_rng(2)
+    x = g.standard_normal((1, 4, 5, 2))
+    w = np.zeros((2, 9, 2))
+    w[0, t, 0] = w[1, t, 1] = 1.0
+    dy, dx = t // 3 - 1, t % 3 - 1
+    y = cr.conv3x3(x, w)
+    for i in range(4):
+        for j in range(5):
+            np.testing.assert_array_equal(y[0, i, j], x[0, (i + dy) % 4, (j + dx) % 5])
+
+
+def test_gradients_are_the_adjoints_of_the_convolution():
+    g = np.random.default_rng(3)
+    x = g.standard_normal((2, 4, 6, 5))
+    w = g.standard_normal((3, 9, 5))
+    r = g.standard_normal((2, 4, 6, 3))
+    lhs = float((cr.conv3x3(x, w) * r).sum())
+    # <conv(x; w), r> = <x, dgrad(r; w)> = <w, wgrad(x, r)>
+    assert lhs == pytest.approx(float((x * cr.conv3x3_dgrad(r, w)).sum()), rel=1e-12)
+    assert lhs == pytest.approx(float((w * cr.conv3x3_wgrad(x, r)).sum()), rel=1e-12)
+
+
+def _net(seed, h=4, w=8):
+    g = np.random.default_rng(seed)
+    weights, biases = [], []
+    for ci, co in cr.LAYERS:
+        weights.append(g.standard_normal((co, 9, ci)) * np.sqrt(2.0 / (9 * ci)))
+        biases.append(g.standard_normal(co) * 0.1)
+    x = np.zeros((1, h, w, 16))
+    x[..., :5] = g.standard_normal((1, h, w, 5))
+    target = np.zeros_like(x)
+    target[..., :5] = g.standard_normal((1, h, w, 5))
+    return x, target, weights, biases
+
+
+def test_network_gradients_match_finite_differences():
+    x, target, weights, biases = _net(4)
+    loss, gw, gb = cr.net_loss_and_grads(x, target, weights, biases)
+    g = np.random.default_rng(5)
+    eps = 1e-6
+    for _ in range(24):
+        l = int(g.integers(0, 6))
+        co, ci = cr.LAYERS[l][1], cr.LAYERS[l][0]
+        if g.random() < 0.75:
+            # weights of real channels only (padding channels carry nothing)
+            o = int(g.integers(0, 5 if l == 5 else co))
+            c = int(g.integers(0, 5 if l == 0 else ci))
+            t = int(g.integers(0, 9))
+            wp = [v.copy() for v in weights]
+            wm = [v.copy() for v in weights]
+            wp[l][o, t, c] += eps
+            wm[l][o, t, c] -= eps
+            fd = (cr.net_loss_and_grads(x, target, wp, biases)[0]
+                  - cr.net_loss_and_grads(x, target, wm, biases)[0]) / (2 * eps)
+            assert gw[l][o, t, c] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+        else:
+            o = int(g.integers(0, 5 if l == 5 else co))
+            bp = [v.copy() for v in biases]
+            bm = [v.copy() for v in biases]
+            bp[l][o] += eps
+            bm[l][o] -= eps
+            fd = (cr.net_loss_and_grads(x, target, weights, bp)[0]
+                  - cr.net_loss_and_grads(x, target, weights, bm)[0]) / (2 * eps)
+            assert gb[l][o] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    assert loss > 0
+
+
+def test_adam_first_step_is_lr_times_the_gradient_sign():
+    g = np.array([3.0, -0.5, 1e-3, -20.0])
+    p1, m, v = cr.adam(np.zeros(4), g, np.zeros(4), np.zeros(4), t=1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(p1, -0.01 * np.sign(g), rtol=1e-12)

@@ -167,3 +167,23 @@ def test_invalid_parameters_are_rejected():
     for bad in (dict(D1=0.0), dict(M=-1.0), dict(rho2=0.0), dict(scalar_q=7), dict(nx=0)):
         with pytest.raises(ValueError):
             oracle.OracleSim(dict(dict(nx=4, ny=4), **bad))
+
+
+def test_restart_from_macros_returns_them():
+    """init_macros puts every population at its equilibrium (Eqs. 24, 29-30, 35);
+    with phi uniform and no force the moments of Eqs. (26), (32), (37) must give
+    back the six fields exactly (to rounding), whatever u, p, c1, c2 are."""
+    import oracle
+    nx, ny = 7, 5
+    g = np.random.default_rng(11)
+    params = dict(nx=nx, ny=ny, sigma=0.01, rho1=1.0, rho2=0.2, mu1=0.1, mu2=0.05,
+                  D1=0.1, D2=0.02, Keq=2.0, A=0.3)
+    s = oracle.OracleSim(params)
+    phi = np.full((ny, nx), 0.3)
+    ux, uy = 0.05 * g.standard_normal((2, ny, nx))
+    p = 1e-3 * g.standard_normal((ny, nx))
+    c1, c2 = g.uniform(0.1, 1.0, (2, ny, nx))
+    s.init_macros(phi, ux, uy, p, c1, c2)
+    f = s.fields()
+    for name, want in (("phi", phi), ("ux", ux), ("uy", uy), ("p", p), ("c1", c1), ("c2", c2)):
+        np.testing.assert_allclose(f[name], want, rtol=1e-12, atol=1e-15, err_msg=name)
