@@ -99,6 +99,12 @@ int lbm_nn_unpack_macros(const float* state, int32_t batch, int32_t h, int32_t w
 int lbm_nn_state_diff(const float* a, const float* b, int32_t batch, int64_t pixels, float* partials,
                       float* out, void* stream);
 
+/* Add independent Gaussian noise of standard deviation sigma to the first `used`
+ * channels of a float state of `pixels` pixels (training-time input corruption);
+ * the draws are a deterministic function of (seed, element). */
+int lbm_nn_add_noise(float* state, int64_t pixels, int32_t used, float sigma, uint32_t seed,
+                     void* stream);
+
 /* Float state -> bfloat16 activation of 16 channels. */
 int lbm_nn_to_bf16(const float* state, int64_t values, void* act, void* stream);
 

@@ -463,6 +463,30 @@ __global__ void state_diff_final(const float* __restrict__ part, int nblk, long 
     out[((size_t)n * 5 + c) * 2 + 1] = (float)sqrt(sm / (double)HW);
 }
 
+// Gaussian noise on the first `used` channels of a float state: Box-Muller
+// (1958) on two uniforms from a counter-based hash (the MurmurHash3 32-bit
+// finalizer) of (seed, element index): reproducible for a given seed.
+__device__ __forceinline__ uint32_t nn_mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__global__ void add_noise_kernel(float* __restrict__ s, long long P, int used, float sigma, uint32_t seed) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P * used;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / used;
+        const int c = (int)(i % used);
+        const uint32_t k = nn_mix32(seed ^ nn_mix32((uint32_t)i ^ (uint32_t)(i >> 32) * 0x9e3779b9u));
+        const float u1 = ((float)(k >> 8) + 1.0f) * 0x1p-24f;  // (0, 1]
+        const float u2 = (float)(nn_mix32(k + 0x68e31da4u) >> 8) * 0x1p-24f;
+        s[p * 16 + c] += sigma * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ s, long long n, __nv_bfloat16* __restrict__ a) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] = __float2bfloat16_rn(s[i]);
@@ -580,6 +604,13 @@ int lbm_nn_state_diff(const float* a, const float* b, int32_t batch, int64_t pix
     constexpr int NBLK = 64;
     state_diff_kernel<<<dim3(NBLK, batch), 256, 0, s>>>(a, b, pixels, partials);
     state_diff_final<<<batch, 32, 0, s>>>(partials, NBLK, pixels, out);
+    return launch_status();
+}
+
+int lbm_nn_add_noise(float* state, int64_t pixels, int32_t used, float sigma, uint32_t seed, void* stream) {
+    if (!state || pixels < 1 || used < 1 || used > 16) return LBM_ERR_ARG;
+    const long long n = (long long)pixels * used;
+    add_noise_kernel<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(state, pixels, used, sigma, seed);
     return launch_status();
 }
 

@@ -56,6 +56,7 @@ def nn_lib():
         "lbm_nn_unpack_macros": [vp, i32, i32, i32, vp, vp, vp, vp, vp],
         "lbm_nn_state_diff": [vp, vp, i32, i64, vp, vp, vp],
         "lbm_nn_to_bf16": [vp, i64, vp, vp],
+        "lbm_nn_add_noise": [vp, i64, i32, f32, ctypes.c_uint32, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -319,8 +320,13 @@ class Surrogate:
                             self.net.s), "unpack")
 
 
-def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, log=print):
-    """Adam on the MSE of one hop over all consecutive snapshot pairs."""
+def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03, log=print):
+    """Adam on the MSE of one hop over all consecutive snapshot pairs, with a
+    cosine learning-rate decay.  The input state is corrupted by Gaussian noise
+    of `noise` (normalised units) while the target stays the solver's: the
+    network learns to pull a perturbed state back, which keeps its own
+    autoregressive rollouts from drifting (input-noise training as in
+    Sanchez-Gonzalez et al. 2020)."""
     import torch
     net = sur.net
     n, S = data.shape[0], data.shape[1]
@@ -331,6 +337,7 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, log=print):
     g = np.random.default_rng(seed)
     steps = epochs * (len(pairs) // batch)
     losses = torch.zeros(max(1, steps), dtype=torch.float64, device=net.device)
+    ident = torch.zeros(8, dtype=torch.float64, device=net.device)
     step = 0
     t0 = time.perf_counter()
     for ep in range(epochs):
@@ -342,8 +349,15 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, log=print):
             kk = torch.from_numpy(sel[:, 1]).to(net.device)
             xf = data[ii, kk].contiguous()
             yf = data[ii, kk + 1].contiguous()
-            sur.pack(xf, ws, ws.x32, ws.x16)
+            sur.pack(xf, ws, ws.x32, None if noise > 0 else ws.x16)
             sur.pack(yf, ws, ws.t32)
+            if noise > 0:
+                _ck(L.lbm_nn_add_noise(_p(ws.x32), ws.P, USED, noise, (seed * 1000003 + step) & 0xffffffff,
+                                       net.s), "noise")
+                _ck(L.lbm_nn_to_bf16(_p(ws.x32), ws.x32.numel(), _p(ws.x16), net.s), "to_bf16")
+            if step < 8:  # the loss of predicting no change, for reference
+                _ck(L.lbm_nn_mse(_p(ws.x32), _p(ws.t32), USED, ws.P, None, _p(ws.loss_part),
+                                 _p(ident[step:step + 1]), net.s), "mse")
             net.forward(ws.x32, ws.x16, ws.y32, ws.acts, batch, H, W)
             _ck(L.lbm_nn_mse(_p(ws.y32), _p(ws.t32), USED, ws.P, _p(ws.dz16), _p(ws.loss_part),
                              _p(losses[step:step + 1]), net.s), "mse")
@@ -353,7 +367,9 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, log=print):
         if log:
             lh = losses[:step].cpu().numpy()
             per = max(1, len(order) // batch)
-            log("epoch %d: loss %.4e (first %.4e)  %.1f s" % (ep, lh[-per:].mean(), lh[0], time.perf_counter() - t0))
+            log("epoch %d: loss %.4e (first %.4e, no-change baseline %.4e)  %.1f s"
+                % (ep, lh[-per:].mean(), lh[0], float(ident[:min(step, 8)].mean()), time.perf_counter() - t0))
+    train.identity_loss = float(ident[:min(step, 8)].mean())
     return losses[:step].cpu().numpy()
 
 
@@ -369,12 +385,16 @@ def field_errors(got5, want5):
 
 
 def rollout(sur: Surrogate, sims, hops, judge_every=0, tol=0.05, keq=None):
-    """Advance the lattices `sims` (one shape, FP32, stepped by one Batch) by
-    `hops` network hops.  With judge_every = m > 0 the solver checks every m-th
-    hop: it restarts from the state the hop started from, runs 16 steps, and its
-    result replaces the network's where their RMS distance (in units of the
-    channel spread) exceeds `tol`.  Returns (fields [B, 5, H, W] on the device,
-    stats)."""
+    """Advance the lattices `sims` (one shape, FP32) by `hops` network hops of
+    16 steps.  With judge_every = m > 0 every m-th hop is checked: the solver
+    restarts from the state that hop started from (lbm_init_macros) and runs
+    16 steps.  If every case's network hop lies within `tol` of the solver's (RMS
+    over the lattice, in units of each channel's spread) the network's state
+    becomes the verified state; otherwise the solver takes over from the last
+    verified state (from its own populations when it produced that state, else
+    restarted from the state's fields), runs up to the current hop, and its
+    result is the new verified state.  The lattices' own states are overwritten.  Returns (fields
+    [B, 5, H, W] on the device: phi, ux, uy, p, C; stats)."""
     import torch
     net = sur.net
     B = len(sims)
@@ -385,44 +405,138 @@ def rollout(sur: Surrogate, sims, hops, judge_every=0, tol=0.05, keq=None):
     for j, s in enumerate(sims):
         s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
     sur.pack(f6, ws, ws.x32, ws.x16)
-    keq_t = torch.tensor([float(s.params["Keq"]) if keq is None else keq[j] for j, s in enumerate(sims)],
-                         dtype=torch.float32, device=net.device)
-    macros = torch.empty((B, 6, H, W), dtype=torch.float64, device=net.device) if judge_every else None
-    lb32 = torch.empty_like(ws.x32) if judge_every else None
-    batch = Batch(sims) if judge_every else None
-    judged = fallbacks = 0
+    stats = {"judged": 0, "fallbacks": 0, "solver_steps": 0}
+    if judge_every:
+        keq_t = torch.tensor([float(s.params["Keq"]) if keq is None else keq[j] for j, s in enumerate(sims)],
+                             dtype=torch.float32, device=net.device)
+        macros = torch.empty((B, 6, H, W), dtype=torch.float64, device=net.device)
+        lb32 = torch.empty_like(ws.x32)
+        ver32 = ws.x32.clone()
+        ver_k = 0
+        # the verified state as the solver's own populations, while it is one the
+        # solver produced (None once a network state has been accepted)
+        ver_pop = [s.get_state(device=True) for s in sims]
+        batch = Batch(sims)
+
+        def solver(steps, out32, state32=None, pops=None):
+            if pops is not None:
+                for s, st in zip(sims, pops):
+                    s.set_state(st)
+            else:
+                _ck(L.lbm_nn_unpack_macros(_p(state32), B, H, W, _p(sur.shift), _p(sur.scale), _p(keq_t),
+                                           _p(macros), net.s), "unpack_macros")
+                for j, s in enumerate(sims):
+                    m = macros[j]
+                    s.init_macros(m[0], m[1], m[2], m[3], m[4], m[5])
+            batch.step(steps)
+            for j, s in enumerate(sims):
+                s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
+            sur.pack(f6, ws, out32)
+            stats["solver_steps"] += steps
+
     for k in range(1, hops + 1):
         sur.hop(ws)
         if judge_every and k % judge_every == 0:
-            _ck(L.lbm_nn_unpack_macros(_p(ws.x32), B, H, W, _p(sur.shift), _p(sur.scale), _p(keq_t), _p(macros),
-                                       net.s), "unpack_macros")
-            for j, s in enumerate(sims):
-                m = macros[j]
-                s.init_macros(m[0], m[1], m[2], m[3], m[4], m[5])
-            batch.step(HOP)
-            for j, s in enumerate(sims):
-                s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
-            sur.pack(f6, ws, lb32)
+            solver(HOP, lb32, state32=ws.x32)
             _ck(L.lbm_nn_state_diff(_p(ws.y32), _p(lb32), B, H * W, _p(ws.diff_part), _p(ws.diff), net.s), "diff")
-            d = ws.diff.view(B, 5, 2).cpu().numpy()
-            judged += B
-            for j in range(B):
-                if float(d[j, :, 1].max()) > tol:
-                    ws.y32[j].copy_(lb32[j])
-                    fallbacks += 1
+            rms = ws.diff.view(B, 5, 2)[:, :, 1].cpu().numpy()
+            stats["judged"] += 1
+            if np.all(np.isfinite(rms)) and float(rms.max()) <= tol:
+                ver32.copy_(ws.y32)
+                ver_pop = None
+            else:
+                # the solver takes over from the last verified state, with its own
+                # populations where it produced that state
+                stats["fallbacks"] += 1
+                solver(HOP * (k - ver_k), ws.y32, state32=ver32, pops=ver_pop)
+                ver32.copy_(ws.y32)
+                ver_pop = [s.get_state(device=True) for s in sims]
+            ver_k = k
         ws.x32, ws.y32 = ws.y32, ws.x32
         _ck(L.lbm_nn_to_bf16(_p(ws.x32), ws.x32.numel(), _p(ws.x16), net.s), "to_bf16")
-    if batch is not None:
+    if judge_every:
         batch.close()
     out5 = torch.empty((B, 5, H, W), dtype=torch.float32, device=net.device)
     sur.unpack(ws.x32, ws, out5)
-    return out5, {"judged": judged, "fallbacks": fallbacks}
+    return out5, stats
+
+
+def conv_flops(B, H, W):
+    """Multiply-adds x 2 of one network hop (padding channels included)."""
+    return 2.0 * B * H * W * 9 * sum(ci * co for ci, co in LAYERS)
+
+
+def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
+    """Speed and error of the network against the solver on `cases` (one shape):
+    the solver alone (batched runner, 16 * hops steps), the network alone (hops
+    hops), and the judged hybrid.  Errors are each field's max difference from
+    the solver's result relative to the field's scale (see field_errors)."""
+    import torch
+    dev = sur.net.device
+    stream = sur.net.stream
+
+    def fresh():
+        sims = [Simulation(w.params, precision="fp32", device=dev) for w in cases]
+        for s, w in zip(sims, cases):
+            s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+        b = Batch(sims)
+        b.set_tiling(128, 32)
+        b.step(warm)
+        b.sync()
+        return sims, b
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return r, e0.elapsed_time(e1) * 1e-3
+
+    H, W = cases[0].params["ny"], cases[0].params["nx"]
+    B = len(cases)
+    # the solver alone
+    sims, b = fresh()
+    _, t_lb = timed(lambda: b.step(HOP * hops))
+    f6 = torch.empty((B, 6, H, W), dtype=torch.float32, device=dev)
+    for j, s in enumerate(sims):
+        s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
+    truth = f6.cpu().numpy()
+    truth5 = np.concatenate([truth[:, :4], truth[:, 4:5] + truth[:, 5:6]], axis=1)
+    b.close()
+    # the network alone (one untimed call first: allocations, first launches)
+    sims, b = fresh()
+    b.close()
+    rollout(sur, sims, 1)
+    (out, _), t_nn = timed(lambda: rollout(sur, sims, hops))
+    err_nn = field_errors(out.cpu().numpy(), truth5)
+    # judged hybrid
+    (out_h, st), t_h = timed(lambda: rollout(sur, sims, hops, judge_every=judge_every, tol=tol))
+    err_h = field_errors(out_h.cpu().numpy(), truth5)
+    cells = B * H * W
+    mlups = lambda t: cells * HOP * hops / t / 1e6
+    # the hop's convolutions alone: achieved tensor throughput
+    ws = Workspace(B, H, W, dev, train=False)
+    sur.hop(ws)
+    _, t_hop = timed(lambda: [sur.hop(ws) for _ in range(hops)])
+    return {
+        "cases": B, "shape": [H, W], "hops": hops, "steps_per_hop": HOP,
+        "solver_s": t_lb, "network_s": t_nn, "hybrid_s": t_h,
+        "solver_mlups": mlups(t_lb), "network_mlups_equiv": mlups(t_nn), "hybrid_mlups_equiv": mlups(t_h),
+        "speedup_network": t_lb / t_nn, "speedup_hybrid": t_lb / t_h,
+        "error_network": err_nn, "error_hybrid": err_h, "judge": dict(st, every=judge_every, tol=tol),
+        "conv_tflops": conv_flops(B, H, W) * hops / t_hop / 1e12,
+    }
 
 
 def main():
     import torch
     ap = argparse.ArgumentParser(description="train or evaluate the surrogate network")
-    ap.add_argument("command", choices=["train"])
+    ap.add_argument("command", choices=["train", "evaluate"])
+    ap.add_argument("--model", default=None, help="evaluate: a saved model (.npz)")
+    ap.add_argument("--eval-cases", type=int, default=64)
+    ap.add_argument("--hops", type=int, default=8)
     ap.add_argument("--trajectories", type=int, default=2000)
     ap.add_argument("--snapshots", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=6)
@@ -432,6 +546,10 @@ def main():
     ap.add_argument("--out", default="surrogate.npz")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
+    if args.command == "evaluate":
+        sur = Surrogate.load(args.model, dev)
+        print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops)))
+        return
     t0 = time.perf_counter()
     data = generate(droplet_cases(args.trajectories, 0, args.side), args.snapshots, dev)
     torch.cuda.synchronize()
@@ -442,7 +560,11 @@ def main():
     losses = train(sur, data, epochs=args.epochs, batch=args.batch, lr=args.lr)
     sur.save(args.out)
     print(json.dumps({"trajectories": args.trajectories, "epochs": args.epochs, "first_loss": float(losses[0]),
-                      "last_loss": float(losses[-100:].mean()), "seconds": time.perf_counter() - t0}))
+                      "last_loss": float(losses[-100:].mean()), "no_change_loss": train.identity_loss,
+                      "seconds": time.perf_counter() - t0}), flush=True)
+    del data
+    torch.cuda.empty_cache()
+    print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops)))
 
 
 if __name__ == "__main__":
