@@ -153,6 +153,19 @@ def droplets8192(nx=8192, ny=8192, steps=1000, **over) -> Workload:
                     {"radii": radii.tolist(), "centres": centres.tolist(), "rho_ratio": ratio})
 
 
+def layered_poiseuille(nx=15, ny=150, G=1e-6, D=0.5, steps=200000, **over) -> Workload:
+    """Layered two-phase channel flow with concentration-dependent viscosity
+    (Sec. IV C 2): walls at both y ends (half-way bounce-back), periodic x,
+    phase 1 (rho 10, mu 1) below the centre line, phase 2 (rho 1, mu 0.1) above,
+    log mu = c1 log mu1 + c2 log mu2 (Eq. 48), K_eq = 1, D1 = D2, c1 = phi,
+    c2 = 0, driven by the body force (G, 0)."""
+    p = dict(BASE, nx=nx, ny=ny, wall_x=0, wall_y=1, sigma=0.01, rho1=10.0, rho2=1.0,
+             mu1=1.0, mu2=0.1, D1=D, D2=D, Keq=1.0, Fx=G, visc_model=1)
+    p.update(over)
+    return Workload("layered_poiseuille", p, sdf_planar_y(nx, ny, (ny - 1) / 2.0), 1.0, 0.0, steps,
+                    {"G": G})
+
+
 def batched(n=256, sides=tuple(range(64, 513, 32)), steps=2000) -> list:
     """n independent droplet cases of uneven sizes (one Workload each)."""
     g = rng(WORKLOAD_INDEX["batched"])

@@ -124,3 +124,23 @@ def test_restart_from_macros_matches_oracle(precision, steps):
     sim.init_macros(phi, ux, uy, p, c1, c2)
     sim.step(steps)
     assert_parity(sim.fields(), o.fields(), TOL[precision], label="restart/%s/%d" % (precision, steps))
+
+
+@pytest.mark.parametrize("rho1,bound", [(1.0, 0.01), (10.0, 0.10)])
+def test_layered_poiseuille_15x150(rho1, bound):
+    """The paper's layered channel (Sec. IV C 2) on the GPU, 15 x 150, run to
+    the steady state (200,000 steps), against the steady profile of the
+    equilibrated scalar with Eq. (48) viscosity (see test_oracle_physics)."""
+    from test_oracle_physics import layered_poiseuille_profile
+    from paper_2402_15752_gb300 import Simulation
+    w = wl.layered_poiseuille(rho1=rho1)
+    sim = Simulation(w.params, precision="fp32")
+    sim.init(w.sdf, 1.0, 0.0)
+    sim.step(w.steps)
+    f = sim.fields()
+    assert np.abs(f["c1"] + f["c2"] - 0.5).max() < 2e-3
+    ux = f["ux"].mean(axis=1)
+    want = layered_poiseuille_profile(w.params, np.arange(float(w.params["ny"])))
+    err = np.abs(ux - want).max() / np.abs(want).max()
+    print("\\nlayered Poiseuille 15x150, rho1 = %g: max error %.3e of u_max" % (rho1, err))
+    assert err < bound

@@ -260,3 +260,47 @@ def test_centred_droplet_keeps_mirror_and_transpose_symmetry():
     assert np.allclose(f["ux"], f["uy"].T, atol=1e-12)
     assert np.allclose(f["p"], f["p"].T, atol=1e-12)
     assert np.allclose(f["c1"], f["c1"].T, atol=1e-12)
+
+
+# ------------------------------------------------------ layered Poiseuille --
+def layered_poiseuille_profile(params, y):
+    """Steady velocity of the layered channel once the scalar has equilibrated
+    (Sec. IV C 2): total scalar 1/2 everywhere, split at the Henry equilibrium
+    (K = 1: c1 = phi / 2, c2 = (1 - phi) / 2), viscosity from Eq. (48), phi the
+    tanh profile of Eq. (2).  The momentum balance of a parallel flow,
+    d/dy (mu du/dy) = -G, integrates to mu du/dy = -G (y - y0); with no slip at
+    both half-way walls y = -1/2 and y = ny - 1/2,
+        u(y) = -G int_{-1/2}^{y} (s - y0) / mu(s) ds,  y0 = int s/mu / int 1/mu.
+    Evaluated by the trapezoid rule on a fine grid (independent of the solver)."""
+    ny, W, G = params["ny"], params["W"], params["Fx"]
+    s = np.linspace(-0.5, ny - 0.5, 200001)
+    phi = 0.5 + 0.5 * np.tanh(2.0 * ((ny - 1) / 2.0 - s) / W)
+    c1, c2 = 0.5 * phi, 0.5 * (1.0 - phi)
+    mu = np.exp(c1 * np.log(params["mu1"]) + c2 * np.log(params["mu2"]))
+    def cumtrapz(f):
+        return np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(s))])
+    y0 = cumtrapz(s / mu)[-1] / cumtrapz(1.0 / mu)[-1]
+    u = -G * cumtrapz((s - y0) / mu)
+    return np.interp(y, s, u)
+
+
+@pytest.mark.parametrize("rho1,bound", [(1.0, 0.02), (10.0, 0.10)])
+def test_layered_poiseuille_with_concentration_dependent_viscosity(rho1, bound):
+    """A shorter channel (ny = 40) so that the FP64 oracle reaches the steady
+    state in seconds; the GPU test runs the paper's 15 x 150.  With equal
+    densities the profile matches to 1.7 % (the diffuse interface); with the
+    paper's density ratio 10 the method as stated deviates by 7.7 %, and the
+    deviation does not shrink with the channel height (8.7 % at ny = 20, 7.2 % at
+    ny = 80, measured), so it is the model's, not the resolution's."""
+    w = wl.layered_poiseuille(nx=4, ny=40, D=0.5, rho1=rho1)
+    s = oracle.OracleSim(w.params)
+    s.init(w.sdf, 1.0, 0.0)
+    s.step(24000)
+    f = s.fields()
+    c = f["c1"] + f["c2"]
+    assert np.abs(c - 0.5).max() < 2e-3  # the scalar has equilibrated
+    ux = f["ux"].mean(axis=1)
+    want = layered_poiseuille_profile(w.params, np.arange(40.0))
+    err = np.abs(ux - want).max() / np.abs(want).max()
+    assert err < bound, err
+    assert np.abs(f["uy"]).max() < 1e-2 * np.abs(want).max()  # spurious currents only
