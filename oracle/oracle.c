@@ -102,6 +102,25 @@ static double exchange_source(const orc_params* p, double phi, double c1, double
     return p->A * mixed_diffusivity(p, phi) * (p->Keq * c2 * phi - c1 * (1.0 - phi));
 }
 
+/* One-scalar model (Eq. 31 and the two relations after it), with phi clipped
+ * to [0, 1]: K_eff = K phi + (1 - phi), D_eff = D1 K phi + D2 (1 - phi). */
+static double k_eff(const orc_params* p, double phi) {
+    const double ph = clip01(phi);
+    return p->Keq * ph + (1.0 - ph);
+}
+static double d_eff(const orc_params* p, double phi) {
+    const double ph = clip01(phi);
+    return p->D1 * p->Keq * ph + p->D2 * (1.0 - ph);
+}
+/* c split between the phases at the Henry equilibrium c1/phi = K c2/(1 - phi)
+ * (c1 = K phi c / K_eff, c2 = (1 - phi) c / K_eff): how the one-scalar model
+ * reports c1 and c2 and feeds the viscosity relations. */
+static void henry_split(const orc_params* p, double phi, double c, double* c1, double* c2) {
+    const double ph = clip01(phi), ke = k_eff(p, phi);
+    *c1 = p->Keq * ph * c / ke;
+    *c2 = (1.0 - ph) * c / ke;
+}
+
 /* Eq. (7), Eq. (48), or the exponential scalar relation */
 static double viscosity(const orc_params* p, double phi, double c1, double c2) {
     double mu_lin = clip01(phi) * (p->mu1 - p->mu2) + p->mu2;
@@ -238,7 +257,10 @@ static void zeroth_moments(orc_sim* s) {
             P2 += s->h2[i * N + k];
         }
         s->phi[k] = phi;
-        solve_scalars(&s->p, phi, P1, P2, &s->c1[k], &s->c2[k]);
+        if (s->p.scalar_model == 1)
+            henry_split(&s->p, phi, P1, &s->c1[k], &s->c2[k]);  /* c = sum_i h3_i */
+        else
+            solve_scalars(&s->p, phi, P1, P2, &s->c1[k], &s->c2[k]);
     }
 }
 
@@ -288,6 +310,47 @@ static void macros_of_cell(const orc_sim* s, int x, int y, cell_macros* m) {
     m->tau_g = tau_from_coefficient(m->mu / m->rho);
 }
 
+/* ---- stage 3 for the one-scalar model: f and g as in the two-scalar model,
+ * one lattice h3 for c (Sec. III D):
+ *   h3_0^eq = c + (w_0 - 1) c / K_eff,  h3_i^eq = w_i c / K_eff + w_i c_i.(c u) / cs^2,
+ *   H3_i = w_i c_i . d_t(c u) / cs^2,  tau_h3 = D_eff / (cs^2 dt) + 1/2 (per cell).
+ * The previous-step slot of c1 holds c, the slot of c2 holds 0. */
+static void collide_cell_one_scalar(orc_sim* s, int k, cell_macros* m, double phip, double uxp,
+                                    double uyp, double cp) {
+    const orc_params* p = &s->p;
+    const int N = s->N, qs = p->scalar_q;
+    cell_in* c = &m->in;
+    const double ct = c->c1 + c->c2;  /* c = sum_i h3_i */
+    c->dtpux = (c->phi * c->ux - phip * uxp) / DT;
+    c->dtpuy = (c->phi * c->uy - phip * uyp) / DT;
+    const double dtcux = (ct * c->ux - cp * uxp) / DT, dtcuy = (ct * c->uy - cp * uyp) / DT;
+
+    double* cu = s->cur;
+    cu[0 * N + k] = c->phi;
+    cu[1 * N + k] = c->ux;
+    cu[2 * N + k] = c->uy;
+    cu[3 * N + k] = ct;
+    cu[4 * N + k] = 0.0;
+
+    cell_out o;
+    discrete_functions(p, c, &o);
+    for (int i = 0; i < 9; ++i) {
+        const double fi = s->f[i * N + k], gi = s->g[i * N + k];
+        s->fc[i * N + k] = fi - (fi - o.feq[i]) / s->tau_f + DT * (1.0 - 0.5 / s->tau_f) * o.F[i];
+        s->gc[i * N + k] = gi - (gi - o.geq[i]) / m->tau_g + DT * (1.0 - 0.5 / m->tau_g) * o.G[i];
+    }
+    const double* ws = scalar_weights(qs);
+    const double ke = k_eff(p, c->phi), tau3 = tau_from_coefficient(d_eff(p, c->phi));
+    for (int i = 0; i < qs; ++i) {
+        const double cuv = CX[i] * c->ux + CY[i] * c->uy;
+        const double eq = (i == 0 ? ct + (ws[0] - 1.0) * ct / ke : ws[i] * ct / ke) + ws[i] * cuv * ct / CS2;
+        const double H3 = ws[i] * (CX[i] * dtcux + CY[i] * dtcuy) / CS2;
+        const double a = s->h1[i * N + k];
+        s->h1c[i * N + k] = a - (a - eq) / tau3 + DT * (1.0 - 0.5 / tau3) * H3;
+        s->h2c[i * N + k] = 0.0;
+    }
+}
+
 /* ---- stage 3: BGK collision (Eqs. 23, 28, 34) ---- */
 static void collide_cell(orc_sim* s, int x, int y) {
     const orc_params* p = &s->p;
@@ -300,6 +363,10 @@ static void collide_cell(orc_sim* s, int x, int y) {
     const double* pv = s->prev;
     const double phip = pv[0 * N + k], uxp = pv[1 * N + k], uyp = pv[2 * N + k];
     const double c1p = pv[3 * N + k], c2p = pv[4 * N + k];
+    if (p->scalar_model == 1) {
+        collide_cell_one_scalar(s, k, &m, phip, uxp, uyp, c1p);
+        return;
+    }
     c->dtpux = (c->phi * c->ux - phip * uxp) / DT;
     c->dtpuy = (c->phi * c->uy - phip * uyp) / DT;
     c->dtc1ux = (c->c1 * c->ux - c1p * uxp) / DT;
@@ -362,6 +429,7 @@ orc_sim* orc_create(const orc_params* p) {
     if (!(p->rho1 > 0) || !(p->rho2 > 0) || !(p->mu1 > 0) || !(p->mu2 > 0)) return NULL;
     if (!(p->Keq > 0) || !(p->A >= 0) || !(p->sigma >= 0)) return NULL;
     if (p->visc_model < 0 || p->visc_model > 2) return NULL;
+    if (p->scalar_model != 0 && p->scalar_model != 1) return NULL;
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->p = *p;
@@ -407,16 +475,24 @@ void orc_init_fields(orc_sim* s, const double* phi, const double* c1, const doub
     memset(s->h1, 0, 9 * (size_t)N * sizeof(double));
     memset(s->h2, 0, 9 * (size_t)N * sizeof(double));
     for (int k = 0; k < N; ++k) {
+        for (int i = 0; i < 9; ++i) s->f[i * N + k] = W9[i] * phi[k];
+        s->prev[0 * N + k] = phi[k];
+        s->prev[1 * N + k] = 0.0;
+        s->prev[2 * N + k] = 0.0;
+        if (p->scalar_model == 1) {
+            /* h3 at its equilibrium for c = c1 + c2 (u = 0) */
+            const double c = c1[k] + c2[k], ke = k_eff(p, phi[k]);
+            for (int i = 0; i < qs; ++i) s->h1[i * N + k] = i == 0 ? c + (ws[0] - 1.0) * c / ke : ws[i] * c / ke;
+            s->prev[3 * N + k] = c;
+            s->prev[4 * N + k] = 0.0;
+            continue;
+        }
         /* S_1 at the initial state; h sums to c - dt S/2, so Eq. (37) returns c */
         const double S1 = exchange_source(p, phi[k], c1[k], c2[k]);
-        for (int i = 0; i < 9; ++i) s->f[i * N + k] = W9[i] * phi[k];
         for (int i = 0; i < qs; ++i) {
             s->h1[i * N + k] = ws[i] * (c1[k] - 0.5 * DT * S1);
             s->h2[i * N + k] = ws[i] * (c2[k] + 0.5 * DT * S1);
         }
-        s->prev[0 * N + k] = phi[k];
-        s->prev[1 * N + k] = 0.0;
-        s->prev[2 * N + k] = 0.0;
         s->prev[3 * N + k] = c1[k];
         s->prev[4 * N + k] = c2[k];
     }
@@ -443,13 +519,23 @@ void orc_init_macros(orc_sim* s, const double* phi, const double* ux, const doub
             s->f[i * N + k] = o.feq[i];
             s->g[i * N + k] = o.geq[i];
         }
+        s->prev[0 * N + k] = phi[k];
+        s->prev[1 * N + k] = ux[k];
+        s->prev[2 * N + k] = uy[k];
+        if (p->scalar_model == 1) {
+            const double c = c1[k] + c2[k], ke = k_eff(p, phi[k]);
+            for (int i = 0; i < qs; ++i) {
+                const double cuv = CX[i] * ux[k] + CY[i] * uy[k];
+                s->h1[i * N + k] = (i == 0 ? c + (ws[0] - 1.0) * c / ke : ws[i] * c / ke) + ws[i] * cuv * c / CS2;
+            }
+            s->prev[3 * N + k] = c;
+            s->prev[4 * N + k] = 0.0;
+            continue;
+        }
         for (int i = 0; i < qs; ++i) {
             s->h1[i * N + k] = o.h1eq[i] - ws[i] * 0.5 * DT * S1;
             s->h2[i * N + k] = o.h2eq[i] + ws[i] * 0.5 * DT * S1;
         }
-        s->prev[0 * N + k] = phi[k];
-        s->prev[1 * N + k] = ux[k];
-        s->prev[2 * N + k] = uy[k];
         s->prev[3 * N + k] = c1[k];
         s->prev[4 * N + k] = c2[k];
     }

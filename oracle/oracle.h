@@ -34,6 +34,9 @@ typedef struct {
     int visc_model;       /* 0: linear in phi, 1: log mu = c1 log mu1 + c2 log mu2,
                              2: mu = mu_lin(phi) * exp(-visc_beta * (c1 + c2)) */
     double visc_beta;
+    int scalar_model;     /* 0: two-scalar lattices h1, h2 (Sec. III C);
+                             1: one-scalar lattice h3 for c = c1 + c2 (Sec. III D);
+                             c1, c2 are then reported as the Henry split of c */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
