@@ -67,6 +67,17 @@ extern "C" {
 #define LBM_VISC_LOG_C  1 /* log mu = c1 log mu1 + c2 log mu2          Eq. (48) */
 #define LBM_VISC_EXP_T  2 /* mu = [phi (mu1 - mu2) + mu2] exp(-visc_beta (c1 + c2)) */
 
+/* Scalar transport.  TWO: the two-scalar lattices h1, h2 with the auxiliary
+ * interfacial source (Sec. III C, Eqs. 34-38).  ONE: the one-scalar lattice h3 for
+ * the total c = c1 + c2 (Sec. III D): h3_0^eq = c + (w_0 - 1) c / K_eff,
+ * h3_i^eq = w_i c / K_eff + w_i c_i.(c u) / cs^2, source w_i c_i.d_t(c u) / cs^2,
+ * tau_h3 = D_eff / cs^2 + 1/2 per node, with K_eff = K phi + (1 - phi) and
+ * D_eff = D1 K phi + D2 (1 - phi) (Eq. 31, phi clipped to [0, 1]); c1 and c2 are then
+ * the Henry split c1 = K phi c / K_eff, c2 = (1 - phi) c / K_eff (fields, viscosity).
+ * ONE runs in LBM_FP64 and LBM_FP32, on single lattices (not in a batch). */
+#define LBM_SCALAR_TWO 0
+#define LBM_SCALAR_ONE 1
+
 /* field mask bits for lbm_get_fields; fields are written in this order */
 #define LBM_FIELD_PHI (1u << 0)
 #define LBM_FIELD_UX  (1u << 1)
@@ -101,6 +112,7 @@ typedef struct {
     double Fx, Fy;
     int32_t visc_model;    /* LBM_VISC_*                                             */
     double visc_beta;      /* exponent of LBM_VISC_EXP_T                             */
+    int32_t scalar_model;  /* LBM_SCALAR_TWO or LBM_SCALAR_ONE                       */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

@@ -38,6 +38,10 @@ int validate(const lbm_params* p, char* err, size_t n) {
     if (p->scalar_q != 5 && p->scalar_q != 9) { snprintf(err, n, "scalar_q must be 5 or 9 (got %d)", p->scalar_q); return LBM_ERR_ARG; }
     if (p->precision < LBM_FP64 || p->precision > LBM_FP32_FP16STORE) { snprintf(err, n, "unknown precision %d", p->precision); return LBM_ERR_ARG; }
     if (p->visc_model < LBM_VISC_LINEAR || p->visc_model > LBM_VISC_EXP_T) { snprintf(err, n, "unknown visc_model %d", p->visc_model); return LBM_ERR_ARG; }
+    if (p->scalar_model != LBM_SCALAR_TWO && p->scalar_model != LBM_SCALAR_ONE) { snprintf(err, n, "unknown scalar_model %d", p->scalar_model); return LBM_ERR_ARG; }
+    if (p->scalar_model == LBM_SCALAR_ONE && p->precision != LBM_FP64 && p->precision != LBM_FP32) {
+        snprintf(err, n, "the one-scalar model runs in LBM_FP64 or LBM_FP32"); return LBM_ERR_ARG;
+    }
     if (!finite_pos(p->W)) { snprintf(err, n, "W must be > 0"); return LBM_ERR_ARG; }
     if (!finite_pos(p->rho1) || !finite_pos(p->rho2)) { snprintf(err, n, "rho1, rho2 must be > 0"); return LBM_ERR_ARG; }
     if (!finite_pos(p->Keq)) { snprintf(err, n, "Keq must be > 0"); return LBM_ERR_ARG; }
@@ -181,6 +185,7 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
     h->geo.nx = params->nx; h->geo.ny = params->ny; h->geo.nxb = L.nxb;
     h->geo.wall_x = params->bc_x == LBM_BC_WALL; h->geo.wall_y = params->bc_y == LBM_BC_WALL;
     h->geo.strip_h = params->ny;
+    h->geo.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
     h->cf = coeffs_of<float>(params);
     h->cd = coeffs_of<double>(params);
     h->device = attr.device;

@@ -39,7 +39,8 @@ constexpr int RED_THREADS = 256;
 struct Geometry {
     int nx, ny, nxb;
     int wall_x, wall_y;
-    int strip_h;  // rows per CTA of the step kernel
+    int strip_h;     // rows per CTA of the step kernel
+    int one_scalar;  // one-scalar model: h1 planes hold h3, h2 planes unused
 };
 
 // Per-run constants, derived once on the host in double and cast to the

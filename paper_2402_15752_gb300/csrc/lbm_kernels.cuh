@@ -313,7 +313,8 @@ struct NodeFH {
 };
 
 // Fast pull: interior node at element offset `nd`, upstream offsets `doff`.
-template <int QS, typename T, typename R, bool CG = false>
+// ONE: one-scalar model, the h1 planes hold h3 and the h2 planes are unused.
+template <int QS, typename T, typename R, bool CG = false, bool ONE = false>
 __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long long nd,
                                              const int (&doff)[9], NodeFH<T, R, QS>& P) {
 #pragma unroll
@@ -321,11 +322,11 @@ __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long lon
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
         P.h1[i] = to_r<R>(ld<CG>(src + nd + doff[i] + (18 + i) * 32));
-        P.h2[i] = to_r<R>(ld<CG>(src + nd + doff[i] + (18 + QS + i) * 32));
+        P.h2[i] = ONE ? R(0) : to_r<R>(ld<CG>(src + nd + doff[i] + (18 + QS + i) * 32));
     }
 }
 
-template <int QS, typename T, typename R, bool CG = false>
+template <int QS, typename T, typename R, bool CG = false, bool ONE = false>
 __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geometry& g, int x,
                                             int y, NodeFH<T, R, QS>& P) {
     constexpr int NQ = nq_of(QS);
@@ -339,7 +340,7 @@ __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geo
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
         P.h1[i] = pull_any<NQ, T, R, CG>(src, g, x, y, 18, i);
-        P.h2[i] = pull_any<NQ, T, R, CG>(src, g, x, y, 18 + QS, i);
+        P.h2[i] = ONE ? R(0) : pull_any<NQ, T, R, CG>(src, g, x, y, 18 + QS, i);
     }
 }
 
@@ -372,7 +373,18 @@ __device__ __forceinline__ double phase_value_d(typename PhaseFix<T>::S v) {
     else return double(v);
 }
 
-template <typename T, typename R, int QS>
+// One-scalar model (Eq. 31 and the relations after it), phi clipped to [0, 1]:
+// K_eff = K phi + (1 - phi); c split between the phases at the Henry
+// equilibrium, c1 = K phi c / K_eff, c2 = (1 - phi) c / K_eff.
+template <typename R>
+__device__ __forceinline__ void henry_split(const Coeffs<R>& C, R phi, R c, R& c1, R& c2) {
+    const R ph = phi < R(0) ? R(0) : (phi > R(1) ? R(1) : phi);
+    const R inv = div_r(c, C.K * ph + (R(1) - ph));
+    c1 = C.K * ph * inv;
+    c2 = (R(1) - ph) * inv;
+}
+
+template <typename T, typename R, int QS, bool ONE = false>
 __device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS>& P,
                                        typename PhaseFix<T>::S& phis, R& phi, R& c1, R& c2) {
     phis = phase_sum<T, R, QS>(P);
@@ -384,7 +396,8 @@ __device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS
         P1 += P.h1[i];
         P2 += P.h2[i];
     }
-    solve_scalars(C, phi, omp, P1, P2, c1, c2);
+    if constexpr (ONE) henry_split(C, phi, P1, c1, c2);  // c = sum_i h3_i
+    else solve_scalars(C, phi, omp, P1, P2, c1, c2);
 }
 
 // D2Q9 stencils of phi at the ring centre column X (Eqs. 41-42).  Fixed-point
@@ -475,7 +488,7 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
 // evaluation of the current state (FIELDS = true): the W columns x0 .. x0+W-1
 // (one thread each) of rows ya .. yb-1, marched upwards.  CG selects the load
 // path (see ld).  The caller's block has exactly W threads.
-template <typename T, typename R, int QS, bool FIELDS, int W, bool CG>
+template <typename T, typename R, int QS, bool FIELDS, int W, bool CG, bool ONE = false>
 __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restrict__ dst,
                                            R* __restrict__ prev, const Geometry& g, const Coeffs<R>& C,
                                            unsigned* __restrict__ flag, uint32_t mask,
@@ -516,10 +529,10 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         PS phis;
         R phi, c1, c2;
         if (x_inner && ry >= 1 && ry <= g.ny - 2)
-            pull_fh_fast<QS, T, R, CG>(src, node_off<NQ>(g, x, ry), doff, P);
+            pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQ>(g, x, ry), doff, P);
         else
-            pull_fh_any<QS, T, R, CG>(src, g, rx, ry, P);
-        zeroth<T, R, QS>(C, P, phis, phi, c1, c2);
+            pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
+        zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
         s_phi[yy & 3][tid + 1] = phis;
         s_c[yy & 3][0][tid + 1] = c1;
         s_c[yy & 3][1][tid + 1] = c2;
@@ -528,10 +541,10 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             PS hs;
             R a, b, c;
             if (h_inner && ry >= 1 && ry <= g.ny - 2)
-                pull_fh_fast<QS, T, R, CG>(src, node_off<NQ>(g, hx, ry), doff, hp);
+                pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQ>(g, hx, ry), doff, hp);
             else
-                pull_fh_any<QS, T, R, CG>(src, g, hx, ry, hp);
-            zeroth<T, R, QS>(C, hp, hs, a, b, c);
+                pull_fh_any<QS, T, R, CG, ONE>(src, g, hx, ry, hp);
+            zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
             s_phi[yy & 3][hcol] = hs;
             s_c[yy & 3][0][hcol] = b;
             s_c[yy & 3][1][hcol] = c;
@@ -635,12 +648,13 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 const R d1ux = c1 * ux - pv[3] * pv[1], d1uy = c1 * uy - pv[3] * pv[2];
                 const R d2ux = c2 * ux - pv[4] * pv[1], d2uy = c2 * uy - pv[4] * pv[2];
                 {
+                    // one-scalar model: the c1 slot holds c = c1 + c2, the c2 slot 0
                     R* pp = prev + node_off<5>(g, x, y);
                     pp[0] = phi;
                     pp[32] = ux;
                     pp[64] = uy;
-                    pp[96] = c1;
-                    pp[128] = c2;
+                    pp[96] = ONE ? c1 + c2 : c1;
+                    pp[128] = ONE ? R(0) : c2;
                 }
                 // non-finite values, or phi outside the fixed-point range
                 if (!finite5(phi, ux, uy, c1, c2) || !(phi > R(-1.5) && phi < R(1.5))) atomicOr(flag, 1u);
@@ -678,7 +692,32 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     }
                 }
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
-                {
+                if constexpr (ONE) {
+                    // ---- e3'. h3: one-scalar model (Sec. III D) ----
+                    // h3*_i = h3_i - w3 (h3_i - h3_i^eq) + (1 - w3/2) H3_i with
+                    // tau_h3 = D_eff / cs^2 + 1/2 per node; the rest population takes
+                    // what the moving ones leave of c = sum_i h3_i (exact conservation)
+                    R P1 = R(0), s1 = R(0);
+#pragma unroll
+                    for (int i = 0; i < QS; ++i) P1 += cur.h1[i];
+                    const R ph = phi < R(0) ? R(0) : (phi > R(1) ? R(1) : phi);
+                    const R omp_c = R(1) - ph;
+                    const R w3 = div_r(R(1), R(3) * (C.KD1 * ph + C.D2 * omp_c) + R(0.5));
+                    const R f3 = R(1) - R(0.5) * w3;
+                    const R a3 = w3 * div_r(P1, C.K * ph + omp_c);
+                    const R dcux = P1 * ux - pv[3] * pv[1], dcuy = P1 * uy - pv[3] * pv[2];
+                    const R B3x = R(3) * (w3 * P1 * ux + f3 * dcux), B3y = R(3) * (w3 * P1 * uy + f3 * dcuy);
+                    const R k3 = R(1) - w3;
+#pragma unroll
+                    for (int i = 1; i < QS; ++i) {
+                        const R w = wq<R, QS>(i);
+                        const R cB = (cx(i) ? R(cx(i)) * B3x : R(0)) + (cy(i) ? R(cy(i)) * B3y : R(0));
+                        const T v = store_value<T>(k3 * cur.h1[i] + w * (a3 + cB), pop_key(key, 18 + i));
+                        s1 += to_r<R>(v);
+                        stcs(o + (18 + i) * 32, v);
+                    }
+                    stcs(o + 18 * 32, store_value<T>(P1 - s1, pop_key(key, 18)));
+                } else {
                     const R Dm = mixed_diffusivity(C, phi, omp);
                     const R S1 = C.A * Dm * (C.K * c2 * phi - c1 * omp);
                     const R Ht = Dm * (dphix * (dc1x + C.K * dc2x) + dphiy * (dc1y + C.K * dc2y));
@@ -723,14 +762,14 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 
 // One launch = one step (or one field evaluation) of a single lattice: CTA
 // (bx, by) owns columns bx*STRIP_W .. +STRIP_W-1 of rows by*strip_h .. +strip_h-1.
-template <typename T, typename R, int QS, bool FIELDS>
+template <typename T, typename R, int QS, bool FIELDS, bool ONE = false>
 __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
     strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
                  Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
                  int out_f64) {
     const int ya = blockIdx.y * g.strip_h;
-    strip_tile<T, R, QS, FIELDS, STRIP_W, false>(src, dst, prev, g, C, flag, mask, out, out_f64,
-                                                 blockIdx.x * STRIP_W, ya, min(ya + g.strip_h, g.ny));
+    strip_tile<T, R, QS, FIELDS, STRIP_W, false, ONE>(src, dst, prev, g, C, flag, mask, out, out_f64,
+                                                      blockIdx.x * STRIP_W, ya, min(ya + g.strip_h, g.ny));
 }
 
 // Initial state: populations at the (source-shifted) equilibria of the given
@@ -789,15 +828,27 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
     } else {
         for (int i = 0; i < 9; ++i) put(0, i, w9<double>(i) * phi * (1.0 + 3.0 * cu_of(i)));
     }
+    R* pp = prev + node_off<5>(g, x, y);
+    pp[0] = R(phi);
+    pp[32] = R(ux);
+    pp[64] = R(uy);
+    if (g.one_scalar) {
+        // h3 at the equilibrium of Sec. III D for c = c1 + c2; the h2 planes stay 0
+        const double c = c1 + c2, ke = C.K * phic + (1.0 - phic);
+        for (int i = 0; i < QS; ++i) {
+            const double w = wq<double, QS>(i);
+            put(18, i, (i == 0 ? c + (w - 1.0) * c / ke : w * c / ke) + 3.0 * w * cu_of(i) * c);
+            put(18 + QS, i, 0.0);
+        }
+        pp[96] = R(c);
+        pp[128] = R(0);
+        return;
+    }
     for (int i = 0; i < QS; ++i) {
         const double w = wq<double, QS>(i), e = 1.0 + 3.0 * cu_of(i);
         put(18, i, w * (c1 * e - 0.5 * S1));
         put(18 + QS, i, w * (c2 * e + 0.5 * S1));
     }
-    R* pp = prev + node_off<5>(g, x, y);
-    pp[0] = R(phi);
-    pp[32] = R(ux);
-    pp[64] = R(uy);
     pp[96] = R(c1);
     pp[128] = R(c2);
 }
@@ -824,7 +875,8 @@ __global__ void __launch_bounds__(RED_THREADS)
         }
         double c = 0.0;
         for (int i = 0; i < QS; ++i)
-            c += pull_any<NQ, T, double>(pop, g, x, y, 18, i) + pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i);
+            c += pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
+                 (g.one_scalar ? 0.0 : pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i));
         b += c;
     }
     __shared__ double sa[RED_THREADS / 32], sb[RED_THREADS / 32];
@@ -888,6 +940,17 @@ inline dim3 strip_grid(const Geometry& g) {
 template <typename T, typename R>
 cudaError_t launch_step_impl(const void* src, void* dst, void* prev, const Geometry& g,
                              const Coeffs<R>& C, int q, unsigned* flag, cudaStream_t s) {
+    if constexpr (!IsHalf<T>::value) {
+        if (g.one_scalar) {
+            if (q == 5)
+                strip_kernel<T, R, 5, false, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+                    (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+            else
+                strip_kernel<T, R, 9, false, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+                    (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+            return cudaGetLastError();
+        }
+    }
     if (q == 5)
         strip_kernel<T, R, 5, false><<<strip_grid(g), STRIP_W, 0, s>>>(
             (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
@@ -900,6 +963,17 @@ cudaError_t launch_step_impl(const void* src, void* dst, void* prev, const Geome
 template <typename T, typename R>
 cudaError_t launch_fields_impl(const void* src, const Geometry& g, const Coeffs<R>& C, int q,
                                uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    if constexpr (!IsHalf<T>::value) {
+        if (g.one_scalar) {
+            if (q == 5)
+                strip_kernel<T, R, 5, true, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+                    (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
+            else
+                strip_kernel<T, R, 9, true, true><<<strip_grid(g), STRIP_W, 0, s>>>(
+                    (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
+            return cudaGetLastError();
+        }
+    }
     if (q == 5)
         strip_kernel<T, R, 5, true><<<strip_grid(g), STRIP_W, 0, s>>>(
             (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);

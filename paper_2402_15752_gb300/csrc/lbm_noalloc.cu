@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NA_THREADS)
         }
         for (int i = 0; i < QS; ++i)
             b += lbm::pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
-                 lbm::pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i);
+                 (g.one_scalar ? 0.0 : lbm::pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i));
     }
     __shared__ double sa[NA_THREADS], sb[NA_THREADS];
     __shared__ long long si[NA_THREADS];
@@ -179,6 +179,7 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     g.wall_x = params->bc_x == LBM_BC_WALL;
     g.wall_y = params->bc_y == LBM_BC_WALL;
     g.strip_h = params->ny;
+    g.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = lbm::by_storage(params->precision, [&](auto t, auto) {
         return na_launch<decltype(t)>(d_state, g, qs, scratch, (int)nchunks, s);

@@ -73,6 +73,12 @@ def test_workspace_size_and_validation(L):
         q = lbm.make_params(b, "fp32")
         assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0, b
         assert L.lbm_last_error(None)
+    q = lbm.make_params(dict(nx=4, ny=4, scalar_model=2), "fp32")
+    assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0
+    q = lbm.make_params(dict(nx=4, ny=4, scalar_model=1), "bf16")  # one-scalar: FP64/FP32 only
+    assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0
+    q = lbm.make_params(dict(nx=4, ny=4, scalar_model=1), "fp32")
+    assert L.lbm_workspace_bytes(ctypes.byref(q)) > 0
     for code in (-1, 4):  # precision codes outside LBM_FP64 .. LBM_FP32_FP16STORE
         q = lbm.make_params(dict(nx=4, ny=4), code)
         assert L.lbm_workspace_bytes(ctypes.byref(q)) == 0

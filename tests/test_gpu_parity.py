@@ -142,5 +142,33 @@ def test_layered_poiseuille_15x150(rho1, bound):
     ux = f["ux"].mean(axis=1)
     want = layered_poiseuille_profile(w.params, np.arange(float(w.params["ny"])))
     err = np.abs(ux - want).max() / np.abs(want).max()
-    print("\\nlayered Poiseuille 15x150, rho1 = %g: max error %.3e of u_max" % (rho1, err))
+    print("\nlayered Poiseuille 15x150, rho1 = %g: max error %.3e of u_max" % (rho1, err))
     assert err < bound
+
+
+ONE_SCALAR_CASES = {
+    # (params, init, steps)
+    "droplet64": lambda: (dict(wl.droplet64().params, scalar_model=1),
+                          ("sdf", wl.droplet64().sdf, 1.0, 0.0), 1000),
+    "planar_walls_ratio": lambda: (dict(wl.planar1024(nx=256, ny=8).params, scalar_model=1),
+                                   ("sdf", wl.planar1024(nx=256, ny=8).sdf, 1.0, 0.0), 1000),
+    "bubble_small": lambda: (dict(wl.bubble1024x2048(nx=96, ny=192).params, scalar_model=1, Keq=1.0),
+                             ("sdf", wl.bubble1024x2048(nx=96, ny=192).sdf, 0.0, 1.0), 100),
+    "ragged_q9": lambda: (dict(wl.droplet64(nx=37, ny=23, R=7.0, rho2=0.2, mu2=0.05, scalar_q=9,
+                                            wall_y=1, Keq=2.5, visc_model=1).params, scalar_model=1),
+                          ("sdf", wl.droplet64(nx=37, ny=23, R=7.0).sdf, 0.9, 0.2), 300),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(ONE_SCALAR_CASES))
+def test_one_scalar_model_matches_oracle(name, precision):
+    """The one-scalar h3 lattice (Sec. III D) against the oracle's."""
+    params, init, steps = ONE_SCALAR_CASES[name]()
+    want = run_oracle(params, init, steps).fields()
+    sim = run_gpu(params, init, steps, precision)
+    assert_parity(sim.fields(), want, TOL[precision], label="one-scalar %s/%s" % (name, precision))
+    assert_parity(sim.fields(), want, TOL[precision], names=("rho", "mu"), label=name)
+    c0 = run_gpu(params, init, 0, precision).conserved()
+    c1 = sim.conserved()
+    assert abs(c1[1] - c0[1]) <= (1e-12 if precision == "fp64" else 1e-6) * abs(c0[1])
