@@ -270,6 +270,55 @@ typedef struct {
     double rho, mu, tau_g;
 } cell_macros;
 
+/* Local grad phi (the scheme given after Eq. 39): with D = -tau_f cs^2 dt,
+ * B = 4 M dt phi (1 - phi) / W and C = sum_i c_i f_i - phi u + dt/2 d_t(phi u),
+ * |grad phi| = (-|C| - B) / D and grad phi = C / (D + B / |grad phi|), which
+ * simplifies to grad phi = -C (|C| + B) / (tau_f cs^2 dt |C|) (0 where C = 0).
+ * Reading: u is not known before grad phi (the surface force needs it), so C
+ * uses the previous step's velocity: phi u - dt/2 d_t(phi u) becomes
+ * (phi + phi_prev) u_prev / 2 with the backward difference of d_t. */
+static void local_phi_gradient(const orc_sim* s, int k, double phi, double* gx, double* gy) {
+    const orc_params* p = &s->p;
+    const int N = s->N;
+    double mx = 0.0, my = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        mx += CX[i] * s->f[i * N + k];
+        my += CY[i] * s->f[i * N + k];
+    }
+    const double php = s->prev[0 * N + k], uxp = s->prev[1 * N + k], uyp = s->prev[2 * N + k];
+    const double Cx = mx - 0.5 * (phi + php) * uxp, Cy = my - 0.5 * (phi + php) * uyp;
+    const double B = 4.0 * p->M * DT * phi * (1.0 - phi) / p->W;
+    const double Cn = sqrt(Cx * Cx + Cy * Cy);
+    if (!(Cn > 0.0)) { *gx = 0.0; *gy = 0.0; return; }
+    const double a = -(Cn + B) / (s->tau_f * CS2 * DT * Cn);
+    *gx = a * Cx;
+    *gy = a * Cy;
+}
+
+/* Local grad c1, grad c2 (Eq. 39) from the first moments of h1, h2, once u and
+ * the time derivatives are known; n = grad phi / (|grad phi| + eps) as in the
+ * collision. */
+static void local_scalar_gradients(const orc_sim* s, int k, cell_in* c) {
+    const orc_params* p = &s->p;
+    const int N = s->N, qs = p->scalar_q;
+    double m1x = 0.0, m1y = 0.0, m2x = 0.0, m2y = 0.0;
+    for (int i = 0; i < qs; ++i) {
+        m1x += CX[i] * s->h1[i * N + k];
+        m1y += CY[i] * s->h1[i * N + k];
+        m2x += CX[i] * s->h2[i * N + k];
+        m2y += CY[i] * s->h2[i * N + k];
+    }
+    const double gn = sqrt(c->dphix * c->dphix + c->dphiy * c->dphiy);
+    const double nx = c->dphix / (gn + NORMAL_EPS), ny = c->dphiy / (gn + NORMAL_EPS);
+    const double s1 = p->D1 * 4.0 * (1.0 - c->phi) * c->c1 / p->W;
+    const double s2 = p->D2 * 4.0 * c->phi * c->c2 / p->W;
+    const double d1 = s->tau_h1 * DT * CS2, d2 = s->tau_h2 * DT * CS2;
+    c->dc1x = (-m1x + c->c1 * c->ux - 0.5 * DT * c->dtc1ux + s1 * nx) / d1;
+    c->dc1y = (-m1y + c->c1 * c->uy - 0.5 * DT * c->dtc1uy + s1 * ny) / d1;
+    c->dc2x = (-m2x + c->c2 * c->ux - 0.5 * DT * c->dtc2ux - s2 * nx) / d2;
+    c->dc2y = (-m2y + c->c2 * c->uy - 0.5 * DT * c->dtc2uy - s2 * ny) / d2;
+}
+
 static void macros_of_cell(const orc_sim* s, int x, int y, cell_macros* m) {
     const orc_params* p = &s->p;
     const int N = s->N, k = y * p->nx + x;
@@ -278,7 +327,10 @@ static void macros_of_cell(const orc_sim* s, int x, int y, cell_macros* m) {
     c->phi = s->phi[k];
     c->c1 = s->c1[k];
     c->c2 = s->c2[k];
-    gradient(s, s->phi, x, y, &c->dphix, &c->dphiy);
+    if (p->grad_scheme == 2)
+        local_phi_gradient(s, k, c->phi, &c->dphix, &c->dphiy);
+    else
+        gradient(s, s->phi, x, y, &c->dphix, &c->dphiy);
     c->lap = laplacian(s, s->phi, x, y);
     gradient(s, s->c1, x, y, &c->dc1x, &c->dc1y);
     gradient(s, s->c2, x, y, &c->dc2x, &c->dc2y);
@@ -373,6 +425,7 @@ static void collide_cell(orc_sim* s, int x, int y) {
     c->dtc1uy = (c->c1 * c->uy - c1p * uyp) / DT;
     c->dtc2ux = (c->c2 * c->ux - c2p * uxp) / DT;
     c->dtc2uy = (c->c2 * c->uy - c2p * uyp) / DT;
+    if (p->grad_scheme >= 1) local_scalar_gradients(s, k, c);
 
     double* cu = s->cur;
     cu[0 * N + k] = c->phi;
@@ -430,6 +483,7 @@ orc_sim* orc_create(const orc_params* p) {
     if (!(p->Keq > 0) || !(p->A >= 0) || !(p->sigma >= 0)) return NULL;
     if (p->visc_model < 0 || p->visc_model > 2) return NULL;
     if (p->scalar_model != 0 && p->scalar_model != 1) return NULL;
+    if (p->grad_scheme < 0 || p->grad_scheme > 2) return NULL;
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     if (!s) return NULL;
     s->p = *p;
@@ -601,6 +655,16 @@ void orc_get_stencils(orc_sim* s, double* out) {
             cell_macros m;
             macros_of_cell(s, x, y, &m);
             const int k = y * p->nx + x;
+            if (p->grad_scheme >= 1 && p->scalar_model == 0) {
+                /* the time derivatives the collision would use */
+                cell_in* c = &m.in;
+                const double* pv = s->prev;
+                c->dtc1ux = (c->c1 * c->ux - pv[3 * N + k] * pv[1 * N + k]) / DT;
+                c->dtc1uy = (c->c1 * c->uy - pv[3 * N + k] * pv[2 * N + k]) / DT;
+                c->dtc2ux = (c->c2 * c->ux - pv[4 * N + k] * pv[1 * N + k]) / DT;
+                c->dtc2uy = (c->c2 * c->uy - pv[4 * N + k] * pv[2 * N + k]) / DT;
+                local_scalar_gradients(s, k, c);
+            }
             out[0 * N + k] = m.in.dphix;
             out[1 * N + k] = m.in.dphiy;
             out[2 * N + k] = m.in.lap;

@@ -37,6 +37,10 @@ typedef struct {
     int scalar_model;     /* 0: two-scalar lattices h1, h2 (Sec. III C);
                              1: one-scalar lattice h3 for c = c1 + c2 (Sec. III D);
                              c1, c2 are then reported as the Henry split of c */
+    int grad_scheme;      /* 0: grad phi, grad c1, grad c2 by the stencil of Eq. (41);
+                             1: grad c1, grad c2 by the local scheme of Eq. (39);
+                             2: also grad phi and |grad phi| by the local scheme
+                                (Sec. III C, after Eq. 39); lap phi always Eq. (42) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
