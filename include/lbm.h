@@ -78,6 +78,17 @@ extern "C" {
 #define LBM_SCALAR_TWO 0
 #define LBM_SCALAR_ONE 1
 
+/* Gradients.  STENCIL: grad phi, grad c1, grad c2 by the isotropic stencil of
+ * Eq. (41).  LOCAL_C: grad c1, grad c2 by the local scheme of Eq. (39) (first
+ * moments of h1, h2, with u, d_t(c_k u) and the normal of the step).  LOCAL_ALL:
+ * also grad phi and |grad phi| by the local scheme given after Eq. (39) (first
+ * moment of f), with the previous step's velocity in its C term (the velocity of
+ * the step needs the surface force, which needs grad phi).  The Laplacian is
+ * Eq. (42) in every scheme.  LOCAL_* run in LBM_FP64 and LBM_FP32, single lattices. */
+#define LBM_GRAD_STENCIL   0
+#define LBM_GRAD_LOCAL_C   1
+#define LBM_GRAD_LOCAL_ALL 2
+
 /* field mask bits for lbm_get_fields; fields are written in this order */
 #define LBM_FIELD_PHI (1u << 0)
 #define LBM_FIELD_UX  (1u << 1)
@@ -113,6 +124,7 @@ typedef struct {
     int32_t visc_model;    /* LBM_VISC_*                                             */
     double visc_beta;      /* exponent of LBM_VISC_EXP_T                             */
     int32_t scalar_model;  /* LBM_SCALAR_TWO or LBM_SCALAR_ONE                       */
+    int32_t grad_scheme;   /* LBM_GRAD_STENCIL, LBM_GRAD_LOCAL_C or LBM_GRAD_LOCAL_ALL */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;

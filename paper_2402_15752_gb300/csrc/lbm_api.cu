@@ -39,8 +39,10 @@ int validate(const lbm_params* p, char* err, size_t n) {
     if (p->precision < LBM_FP64 || p->precision > LBM_FP32_FP16STORE) { snprintf(err, n, "unknown precision %d", p->precision); return LBM_ERR_ARG; }
     if (p->visc_model < LBM_VISC_LINEAR || p->visc_model > LBM_VISC_EXP_T) { snprintf(err, n, "unknown visc_model %d", p->visc_model); return LBM_ERR_ARG; }
     if (p->scalar_model != LBM_SCALAR_TWO && p->scalar_model != LBM_SCALAR_ONE) { snprintf(err, n, "unknown scalar_model %d", p->scalar_model); return LBM_ERR_ARG; }
-    if (p->scalar_model == LBM_SCALAR_ONE && p->precision != LBM_FP64 && p->precision != LBM_FP32) {
-        snprintf(err, n, "the one-scalar model runs in LBM_FP64 or LBM_FP32"); return LBM_ERR_ARG;
+    if (p->grad_scheme < LBM_GRAD_STENCIL || p->grad_scheme > LBM_GRAD_LOCAL_ALL) { snprintf(err, n, "unknown grad_scheme %d", p->grad_scheme); return LBM_ERR_ARG; }
+    if ((p->scalar_model != LBM_SCALAR_TWO || p->grad_scheme != LBM_GRAD_STENCIL) && p->precision != LBM_FP64 &&
+        p->precision != LBM_FP32) {
+        snprintf(err, n, "the one-scalar model and the local gradient schemes run in LBM_FP64 or LBM_FP32"); return LBM_ERR_ARG;
     }
     if (!finite_pos(p->W)) { snprintf(err, n, "W must be > 0"); return LBM_ERR_ARG; }
     if (!finite_pos(p->rho1) || !finite_pos(p->rho2)) { snprintf(err, n, "rho1, rho2 must be > 0"); return LBM_ERR_ARG; }
@@ -90,6 +92,7 @@ lbm::Coeffs<R> coeffs_of(const lbm_params* p) {
     C.log_mu1 = R(std::log(p->mu1)); C.log_mu2 = R(std::log(p->mu2));
     C.visc_beta = R(p->visc_beta);
     C.D1D2 = R(p->D1 * p->D2); C.KD1 = R(p->Keq * p->D1); C.D2 = R(p->D2); C.K = R(p->Keq);
+    C.D1 = R(p->D1); C.M = R(p->M);
     C.halfA = R(0.5 * p->A); C.A = R(p->A);
     C.four_over_W = R(4.0 / p->W);
     C.gx = R(p->gx); C.gy = R(p->gy); C.g_rho_ref = R(p->g_rho_ref);
@@ -186,6 +189,7 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
     h->geo.wall_x = params->bc_x == LBM_BC_WALL; h->geo.wall_y = params->bc_y == LBM_BC_WALL;
     h->geo.strip_h = params->ny;
     h->geo.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
+    h->geo.grad_scheme = params->grad_scheme;
     h->cf = coeffs_of<float>(params);
     h->cd = coeffs_of<double>(params);
     h->device = attr.device;

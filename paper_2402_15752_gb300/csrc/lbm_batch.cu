@@ -53,7 +53,10 @@ int check_cases(lbm_handle* const* cases, int n, char* err, size_t len) {
         const lbm_handle* h = cases[i];
         if (!h) { snprintf(err, len, "case %d is NULL", i); return LBM_ERR_ARG; }
         if (h->p.precision != LBM_FP32) { snprintf(err, len, "case %d: the batched runner takes LBM_FP32 lattices", i); return LBM_ERR_ARG; }
-        if (h->p.scalar_model != LBM_SCALAR_TWO) { snprintf(err, len, "case %d: the batched runner takes the two-scalar model", i); return LBM_ERR_ARG; }
+        if (h->p.scalar_model != LBM_SCALAR_TWO || h->p.grad_scheme != LBM_GRAD_STENCIL) {
+            snprintf(err, len, "case %d: the batched runner takes the two-scalar model with stencil gradients", i);
+            return LBM_ERR_ARG;
+        }
         if (h->p.scalar_q != cases[0]->p.scalar_q) { snprintf(err, len, "case %d: all cases must share scalar_q", i); return LBM_ERR_ARG; }
         if (h->device != cases[0]->device) { snprintf(err, len, "case %d: all cases must be on one device", i); return LBM_ERR_ARG; }
         if (h->stream != cases[0]->stream) { snprintf(err, len, "case %d: all cases must share one stream", i); return LBM_ERR_ARG; }

@@ -86,7 +86,7 @@ struct lbm_handle {
         return lbm::by_storage(p.precision, [&](auto t, auto r) {
             using T = decltype(t);
             using R = decltype(r);
-            return lbm::launch_fields<T, R>(pop(from), geo, coeffs<R>(), p.scalar_q, mask, out, out_f64, s);
+            return lbm::launch_fields<T, R>(pop(from), prev(), geo, coeffs<R>(), p.scalar_q, mask, out, out_f64, s);
         });
     }
 

@@ -41,7 +41,11 @@ struct Geometry {
     int wall_x, wall_y;
     int strip_h;     // rows per CTA of the step kernel
     int one_scalar;  // one-scalar model: h1 planes hold h3, h2 planes unused
+    int grad_scheme; // 0: stencils (Eq. 41); 1: local grad c (Eq. 39); 2: also local grad phi
 };
+
+// Model variant of the step kernel: bit 0 one-scalar, bits 1-2 gradient scheme.
+inline int variant_of(const Geometry& g) { return (g.one_scalar ? 1 : 0) | (g.grad_scheme << 1); }
 
 // Per-run constants, derived once on the host in double and cast to the
 // compute type R (float or double).
@@ -55,6 +59,7 @@ struct Coeffs {
     R mu2, dmu;              // linear viscosity mu2 + dmu * phi
     R log_mu1, log_mu2, visc_beta;
     R D1D2, KD1, D2, K;      // D_m = D1 D2 / (K D1 (1 - phi) + D2 phi)
+    R D1, M;                 // diffusivity of scalar 1, mobility (local gradient schemes)
     R halfA, A;
     R four_over_W;
     R gx, gy, g_rho_ref, Fx, Fy;
@@ -86,10 +91,18 @@ cudaError_t launch_step(const void* src, void* dst, void* prev, const Geometry& 
                         const Coeffs<R>& C, int scalar_q, unsigned* flag, cudaStream_t s);
 
 // Macroscopic fields of the state in `src` (no collision), written as dense
-// nx*ny arrays in mask-bit order (double or float).
+// nx*ny arrays in mask-bit order (double or float); `prev` (the previous-step
+// macros) is read by the local grad phi scheme only.
 template <typename T, typename R>
-cudaError_t launch_fields(const void* src, const Geometry& geo, const Coeffs<R>& C, int scalar_q,
-                          uint32_t mask, void* out, int out_f64, cudaStream_t s);
+cudaError_t launch_fields(const void* src, const void* prev, const Geometry& geo, const Coeffs<R>& C,
+                          int scalar_q, uint32_t mask, void* out, int out_f64, cudaStream_t s);
+
+// The step or field evaluation of a model variant (variant_of(geo) != 0), FP32
+// and FP64 only (lbm_step_var_f32.cu, lbm_step_var_f64.cu).
+template <typename T, typename R>
+cudaError_t launch_variant(const void* src, void* dst, void* prev, const Geometry& geo, const Coeffs<R>& C,
+                           int scalar_q, unsigned* flag, uint32_t mask, void* out, int out_f64, bool fields,
+                           cudaStream_t s);
 
 // Macroscopic fields of an initial state: dense nx*ny double arrays; ux, uy, p
 // may be NULL (zero).

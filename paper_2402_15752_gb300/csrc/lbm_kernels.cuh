@@ -488,7 +488,10 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
 // evaluation of the current state (FIELDS = true): the W columns x0 .. x0+W-1
 // (one thread each) of rows ya .. yb-1, marched upwards.  CG selects the load
 // path (see ld).  The caller's block has exactly W threads.
-template <typename T, typename R, int QS, bool FIELDS, int W, bool CG, bool ONE = false>
+// VAR: model variant, bit 0 = one-scalar model, bits 1-2 = gradient scheme
+// (0: stencils of Eq. 41; 1: local grad c1, grad c2 of Eq. 39; 2: also the local
+// grad phi).  VAR = 0 is the paper's default configuration.
+template <typename T, typename R, int QS, bool FIELDS, int W, bool CG, int VAR = 0>
 __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restrict__ dst,
                                            R* __restrict__ prev, const Geometry& g, const Coeffs<R>& C,
                                            unsigned* __restrict__ flag, uint32_t mask,
@@ -496,6 +499,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                                            int yb) {
     constexpr int NQ = nq_of(QS);
     constexpr int W2 = W + 2;
+    constexpr bool ONE = (VAR & 1) != 0;
+    constexpr int GS = VAR >> 1;
     using PS = typename PhaseFix<T>::S;
     __shared__ PS s_phi[4][W2];
     __shared__ R s_c[4][2][W2];
@@ -568,7 +573,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(pull_any<NQ, T, R, CG>(src, g, x, y, 9, i));
             }
-            if constexpr (!FIELDS) {
+            if constexpr (!FIELDS || GS == 2) {
                 const R* pp = prev + node_off<5>(g, x, y);
 #pragma unroll
                 for (int k = 0; k < 5; ++k) pv[k] = CG ? __ldcg(pp + k * 32) : pp[k * 32];
@@ -584,7 +589,32 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             const int X = tid + 1;
             const PhiStencil<T, R> st = phi_stencil<T, R, W2>(s_phi[(y - 1) & 3], s_phi[y & 3],
                                                               s_phi[(y + 1) & 3], X);
-            const R phi = st.phi, omp = st.omp, dphix = st.dx, dphiy = st.dy, lap = st.lap;
+            const R phi = st.phi, omp = st.omp, lap = st.lap;
+            R dphix = st.dx, dphiy = st.dy;
+            if constexpr (GS == 2) {
+                // local grad phi (the scheme after Eq. 39): C = sum_i c_i f_i - (phi +
+                // phi_prev) u_prev / 2 (the previous step's velocity: u needs the
+                // surface force, which needs grad phi), B = 4 M phi (1 - phi) / W,
+                // grad phi = -C (|C| + B) / (tau_f cs^2 |C|) = -3 w_f C (|C| + B) / |C|
+                R mx, my;
+                if constexpr (PhaseFix<T>::on) {
+                    // fixed point: the w_i / 2 offsets cancel in the first moment
+                    const int ix = (cur.f[1] - cur.f[3]) + ((cur.f[5] - cur.f[7]) + (cur.f[8] - cur.f[6]));
+                    const int iy = (cur.f[2] - cur.f[4]) + ((cur.f[5] - cur.f[7]) + (cur.f[6] - cur.f[8]));
+                    mx = R(ix) * R(FIX_EPS);
+                    my = R(iy) * R(FIX_EPS);
+                } else {
+                    mx = (R(cur.f[1]) - R(cur.f[3])) + ((R(cur.f[5]) - R(cur.f[7])) + (R(cur.f[8]) - R(cur.f[6])));
+                    my = (R(cur.f[2]) - R(cur.f[4])) + ((R(cur.f[5]) - R(cur.f[7])) + (R(cur.f[6]) - R(cur.f[8])));
+                }
+                const R hp = R(0.5) * (phi + pv[0]);
+                const R Cx = mx - hp * pv[1], Cy = my - hp * pv[2];
+                const R Cn = norm_r(Cx, Cy);
+                const R B = C.M * C.four_over_W * phi * omp;
+                const R a = Cn > R(0) ? -R(3) * C.omega_f * div_r(Cn + B, Cn) : R(0);
+                dphix = a * Cx;
+                dphiy = a * Cy;
+            }
             const R(*rs)[W2] = s_c[(y - 1) & 3];
             const R(*r0)[W2] = s_c[y & 3];
             const R(*rn)[W2] = s_c[(y + 1) & 3];
@@ -718,6 +748,21 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     }
                     stcs(o + 18 * 32, store_value<T>(P1 - s1, pop_key(key, 18)));
                 } else {
+                    if constexpr (GS >= 1) {
+                        // local grad c1, grad c2 (Eq. 39) from the first moments of h1, h2
+                        R m1x = R(0), m1y = R(0), m2x = R(0), m2y = R(0);
+#pragma unroll
+                        for (int i = 1; i < QS; ++i) {
+                            if (cx(i)) { m1x += R(cx(i)) * cur.h1[i]; m2x += R(cx(i)) * cur.h2[i]; }
+                            if (cy(i)) { m1y += R(cy(i)) * cur.h1[i]; m2y += R(cy(i)) * cur.h2[i]; }
+                        }
+                        const R s1n = C.D1 * C.four_over_W * omp * c1, s2n = C.D2 * C.four_over_W * phi * c2;
+                        const R k1 = R(3) * C.omega_h1, k2 = R(3) * C.omega_h2;  // 1 / (tau cs^2)
+                        dc1x = k1 * (-m1x + c1 * ux - R(0.5) * d1ux + s1n * nxv);
+                        dc1y = k1 * (-m1y + c1 * uy - R(0.5) * d1uy + s1n * nyv);
+                        dc2x = k2 * (-m2x + c2 * ux - R(0.5) * d2ux - s2n * nxv);
+                        dc2y = k2 * (-m2y + c2 * uy - R(0.5) * d2uy - s2n * nyv);
+                    }
                     const R Dm = mixed_diffusivity(C, phi, omp);
                     const R S1 = C.A * Dm * (C.K * c2 * phi - c1 * omp);
                     const R Ht = Dm * (dphix * (dc1x + C.K * dc2x) + dphiy * (dc1y + C.K * dc2y));
@@ -762,13 +807,13 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 
 // One launch = one step (or one field evaluation) of a single lattice: CTA
 // (bx, by) owns columns bx*STRIP_W .. +STRIP_W-1 of rows by*strip_h .. +strip_h-1.
-template <typename T, typename R, int QS, bool FIELDS, bool ONE = false>
+template <typename T, typename R, int QS, bool FIELDS, int VAR = 0>
 __global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
     strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
                  Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
                  int out_f64) {
     const int ya = blockIdx.y * g.strip_h;
-    strip_tile<T, R, QS, FIELDS, STRIP_W, false, ONE>(src, dst, prev, g, C, flag, mask, out, out_f64,
+    strip_tile<T, R, QS, FIELDS, STRIP_W, false, VAR>(src, dst, prev, g, C, flag, mask, out, out_f64,
                                                       blockIdx.x * STRIP_W, ya, min(ya + g.strip_h, g.ny));
 }
 
@@ -941,15 +986,7 @@ template <typename T, typename R>
 cudaError_t launch_step_impl(const void* src, void* dst, void* prev, const Geometry& g,
                              const Coeffs<R>& C, int q, unsigned* flag, cudaStream_t s) {
     if constexpr (!IsHalf<T>::value) {
-        if (g.one_scalar) {
-            if (q == 5)
-                strip_kernel<T, R, 5, false, true><<<strip_grid(g), STRIP_W, 0, s>>>(
-                    (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
-            else
-                strip_kernel<T, R, 9, false, true><<<strip_grid(g), STRIP_W, 0, s>>>(
-                    (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
-            return cudaGetLastError();
-        }
+        if (variant_of(g)) return launch_variant<T, R>(src, dst, prev, g, C, q, flag, 0u, nullptr, 0, false, s);
     }
     if (q == 5)
         strip_kernel<T, R, 5, false><<<strip_grid(g), STRIP_W, 0, s>>>(
@@ -961,18 +998,12 @@ cudaError_t launch_step_impl(const void* src, void* dst, void* prev, const Geome
 }
 
 template <typename T, typename R>
-cudaError_t launch_fields_impl(const void* src, const Geometry& g, const Coeffs<R>& C, int q,
-                               uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+cudaError_t launch_fields_impl(const void* src, const void* prev, const Geometry& g, const Coeffs<R>& C,
+                               int q, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
     if constexpr (!IsHalf<T>::value) {
-        if (g.one_scalar) {
-            if (q == 5)
-                strip_kernel<T, R, 5, true, true><<<strip_grid(g), STRIP_W, 0, s>>>(
-                    (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
-            else
-                strip_kernel<T, R, 9, true, true><<<strip_grid(g), STRIP_W, 0, s>>>(
-                    (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
-            return cudaGetLastError();
-        }
+        if (variant_of(g))
+            return launch_variant<T, R>(src, nullptr, const_cast<void*>(prev), g, C, q, nullptr, mask, out,
+                                        out_f64, true, s);
     }
     if (q == 5)
         strip_kernel<T, R, 5, true><<<strip_grid(g), STRIP_W, 0, s>>>(
@@ -980,6 +1011,30 @@ cudaError_t launch_fields_impl(const void* src, const Geometry& g, const Coeffs<
     else
         strip_kernel<T, R, 9, true><<<strip_grid(g), STRIP_W, 0, s>>>(
             (const T*)src, nullptr, nullptr, g, C, nullptr, mask, out, out_f64);
+    return cudaGetLastError();
+}
+
+// Launch of a model variant (one-scalar model and/or local gradients), for the
+// step (FIELDS = false) or the field evaluation; compiled in its own units.
+template <typename T, typename R, int VAR>
+cudaError_t launch_variant_impl(const void* src, void* dst, void* prev, const Geometry& g, const Coeffs<R>& C,
+                                int q, unsigned* flag, uint32_t mask, void* out, int out_f64, bool fields,
+                                cudaStream_t s) {
+    if (fields) {
+        if (q == 5)
+            strip_kernel<T, R, 5, true, VAR><<<strip_grid(g), STRIP_W, 0, s>>>(
+                (const T*)src, nullptr, (R*)prev, g, C, nullptr, mask, out, out_f64);
+        else
+            strip_kernel<T, R, 9, true, VAR><<<strip_grid(g), STRIP_W, 0, s>>>(
+                (const T*)src, nullptr, (R*)prev, g, C, nullptr, mask, out, out_f64);
+    } else {
+        if (q == 5)
+            strip_kernel<T, R, 5, false, VAR><<<strip_grid(g), STRIP_W, 0, s>>>(
+                (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+        else
+            strip_kernel<T, R, 9, false, VAR><<<strip_grid(g), STRIP_W, 0, s>>>(
+                (const T*)src, (T*)dst, (R*)prev, g, C, flag, 0u, nullptr, 0);
+    }
     return cudaGetLastError();
 }
 

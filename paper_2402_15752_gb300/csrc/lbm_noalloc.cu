@@ -180,6 +180,7 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     g.wall_y = params->bc_y == LBM_BC_WALL;
     g.strip_h = params->ny;
     g.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
+    g.grad_scheme = params->grad_scheme;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = lbm::by_storage(params->precision, [&](auto t, auto) {
         return na_launch<decltype(t)>(d_state, g, qs, scratch, (int)nchunks, s);

@@ -11,9 +11,9 @@ cudaError_t launch_step<__half, float>(const void* src, void* dst, void* prev, c
 }
 
 template <>
-cudaError_t launch_fields<__half, float>(const void* src, const Geometry& g, const Coeffs<float>& C, int q,
-                                  uint32_t mask, void* out, int out_f64, cudaStream_t s) {
-    return launch_fields_impl<__half, float>(src, g, C, q, mask, out, out_f64, s);
+cudaError_t launch_fields<__half, float>(const void* src, const void* prev, const Geometry& g, const Coeffs<float>& C,
+                                  int q, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    return launch_fields_impl<__half, float>(src, prev, g, C, q, mask, out, out_f64, s);
 }
 
 template <>

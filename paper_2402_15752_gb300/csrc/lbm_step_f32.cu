@@ -11,9 +11,9 @@ cudaError_t launch_step<float, float>(const void* src, void* dst, void* prev, co
 }
 
 template <>
-cudaError_t launch_fields<float, float>(const void* src, const Geometry& g, const Coeffs<float>& C, int q,
-                                  uint32_t mask, void* out, int out_f64, cudaStream_t s) {
-    return launch_fields_impl<float, float>(src, g, C, q, mask, out, out_f64, s);
+cudaError_t launch_fields<float, float>(const void* src, const void* prev, const Geometry& g, const Coeffs<float>& C,
+                                  int q, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    return launch_fields_impl<float, float>(src, prev, g, C, q, mask, out, out_f64, s);
 }
 
 template <>

@@ -11,9 +11,9 @@ cudaError_t launch_step<double, double>(const void* src, void* dst, void* prev, 
 }
 
 template <>
-cudaError_t launch_fields<double, double>(const void* src, const Geometry& g, const Coeffs<double>& C, int q,
-                                  uint32_t mask, void* out, int out_f64, cudaStream_t s) {
-    return launch_fields_impl<double, double>(src, g, C, q, mask, out, out_f64, s);
+cudaError_t launch_fields<double, double>(const void* src, const void* prev, const Geometry& g, const Coeffs<double>& C,
+                                  int q, uint32_t mask, void* out, int out_f64, cudaStream_t s) {
+    return launch_fields_impl<double, double>(src, prev, g, C, q, mask, out, out_f64, s);
 }
 
 template <>

@@ -50,7 +50,7 @@ class LBMParams(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double), ("g_rho_ref", ctypes.c_double),
         ("Fx", ctypes.c_double), ("Fy", ctypes.c_double),
         ("visc_model", ctypes.c_int32), ("visc_beta", ctypes.c_double),
-        ("scalar_model", ctypes.c_int32),
+        ("scalar_model", ctypes.c_int32), ("grad_scheme", ctypes.c_int32),
     ]
 
 
@@ -115,7 +115,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 DEFAULTS = dict(wall_x=0, wall_y=0, scalar_q=5, W=4.0, M=0.01, sigma=0.0,
                 rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, D1=0.1, D2=0.1, Keq=1.0, A=0.1,
                 gx=0.0, gy=0.0, g_rho_ref=0.0, Fx=0.0, Fy=0.0, visc_model=0, visc_beta=0.0,
-                scalar_model=0)
+                scalar_model=0, grad_scheme=0)
 
 
 def make_params(params: dict, precision: str = "fp32") -> LBMParams:
@@ -133,6 +133,7 @@ def make_params(params: dict, precision: str = "fp32") -> LBMParams:
         setattr(s, k, float(q[k]))
     s.visc_model = int(q["visc_model"])
     s.scalar_model = int(q["scalar_model"])
+    s.grad_scheme = int(q["grad_scheme"])
     return s
 
 

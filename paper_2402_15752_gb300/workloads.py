@@ -93,7 +93,7 @@ def sdf_planar_y(nx, ny, y0):
 BASE = dict(wall_x=0, wall_y=0, scalar_q=5, W=4.0, M=0.01, sigma=0.0,
             rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, D1=0.1, D2=0.1, Keq=1.0, A=0.1,
             gx=0.0, gy=0.0, g_rho_ref=0.0, Fx=0.0, Fy=0.0, visc_model=0, visc_beta=0.0,
-            scalar_model=0)
+            scalar_model=0, grad_scheme=0)
 
 
 @dataclass
