@@ -22,6 +22,16 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Four 8x8 bfloat16 matrices from shared memory, one row address per lane
+// (lanes 8m .. 8m+7 give the rows of matrix m): thread t receives row t/4,
+// columns 2(t%4) and 2(t%4)+1 of each matrix -- the mma.m16n8k16 fragment layout.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const uint32_t* row_addr) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(row_addr));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo -> low 16 bits
     return *reinterpret_cast<const uint32_t*>(&v);
@@ -67,7 +77,8 @@ __global__ void __launch_bounds__(CONV_THREADS)
     conv3x3_kernel(const uint32_t* __restrict__ x, const uint32_t* __restrict__ w, const float* __restrict__ bias,
                    void* __restrict__ y, const float* __restrict__ res, const uint32_t* __restrict__ mask,
                    int B, int H, int W) {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
+    static_assert(CI % 16 == 0 && CO % 16 == 0, "k steps of 16 and pairs of n tiles");
     constexpr int IW = in_words<CI>(), WW = w_words<CI>(), CW = CI / 2, KW = 9 * CI / 2;
     uint32_t* s_w = smem;
     uint32_t* s_in = smem + CO * WW;
@@ -97,6 +108,14 @@ __global__ void __launch_bounds__(CONV_THREADS)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[m][j][q] = 0.0f;
 
+        // ldmatrix row addresses: lane l serves matrix l / 8, row l % 8.
+        //   A (pixels x channels): matrix m covers pixels 8 (m & 1) .. +7 and
+        //   channels 8 (m >> 1) .. +7 of the k16 step;
+        //   B (couts x k, k contiguous): matrices 2q, 2q+1 cover couts
+        //   8 (j + q) .. +7 with k 0..7 and 8..15, for n tiles j, j + 1.
+        const int lm = lane >> 3, lr = lane & 7;
+        const int a_pix = lr + 8 * (lm & 1), a_kw = 4 * (lm >> 1);
+        const int b_n = lr + 8 * (lm >> 1), b_kw = 4 * (lm & 1);
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int dy = t / 3 - 1, dx = t % 3 - 1;
@@ -104,22 +123,19 @@ __global__ void __launch_bounds__(CONV_THREADS)
             for (int c0 = 0; c0 < CI; c0 += 16) {
                 uint32_t a[2][4];
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const uint32_t* rowp = s_in + (2 * warp + m + dy + 1) * (TCOLS + 2) * IW;
-                    const uint32_t* p0 = rowp + (g + dx + 1) * IW + c0 / 2;
-                    const uint32_t* p1 = rowp + (g + 8 + dx + 1) * IW + c0 / 2;
-                    a[m][0] = p0[tig];
-                    a[m][1] = p1[tig];
-                    a[m][2] = p0[4 + tig];
-                    a[m][3] = p1[4 + tig];
-                }
+                for (int m = 0; m < 2; ++m)
+                    ldmatrix_x4(a[m], s_in + ((2 * warp + m + dy + 1) * (TCOLS + 2) + a_pix + dx + 1) * IW +
+                                          c0 / 2 + a_kw);
                 const int kw = (t * CI + c0) / 2;
 #pragma unroll
-                for (int j = 0; j < CO / 8; ++j) {
-                    const uint32_t* wp = s_w + (j * 8 + g) * WW + kw;
-                    const uint32_t b[2] = {wp[tig], wp[4 + tig]};
-                    mma_bf16_16816(acc[0][j], a[0], b);
-                    mma_bf16_16816(acc[1][j], a[1], b);
+                for (int j = 0; j < CO / 8; j += 2) {
+                    uint32_t bq[4];
+                    ldmatrix_x4(bq, s_w + (j * 8 + b_n) * WW + kw + b_kw);
+                    const uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+                    mma_bf16_16816(acc[0][j], a[0], b0);
+                    mma_bf16_16816(acc[1][j], a[1], b0);
+                    mma_bf16_16816(acc[0][j + 1], a[0], b1);
+                    mma_bf16_16816(acc[1][j + 1], a[1], b1);
                 }
             }
         }
