@@ -59,7 +59,9 @@ int launch_status() {
 // weight fragment).  GEMM view: M = pixels, N = cout, K = 9 taps x cin.  The
 // weights (all of them) and the tile's input with a one-pixel periodic halo are
 // staged in shared memory; rows are padded by 4 words so that the fragment loads
-// are free of bank conflicts.  Persistent CTAs loop over the tiles.
+// are free of bank conflicts.  Persistent CTAs loop over the tiles; the input of
+// the next tile is copied asynchronously (cp.async, two buffers) while the
+// current one is computed, so that the tensor cores do not wait for it.
 constexpr int CONV_THREADS = 128;
 constexpr int TROWS = 8, TCOLS = 16;
 
@@ -67,10 +69,22 @@ template <int CI>
 constexpr int in_words() { return CI / 2 + 4; }
 template <int CI>
 constexpr int w_words() { return 9 * CI / 2 + 4; }
+template <int CI>
+constexpr int tile_words() { return (TROWS + 2) * (TCOLS + 2) * in_words<CI>(); }
 template <int CI, int CO>
 constexpr size_t conv_smem() {
-    return sizeof(uint32_t) * ((size_t)CO * w_words<CI>() + (size_t)(TROWS + 2) * (TCOLS + 2) * in_words<CI>());
+    return sizeof(uint32_t) * ((size_t)CO * w_words<CI>() + 2 * (size_t)tile_words<CI>());
 }
+
+__device__ __forceinline__ void cp_async16(uint32_t* dst, const uint32_t* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(CONV_THREADS)
@@ -80,25 +94,45 @@ __global__ void __launch_bounds__(CONV_THREADS)
     extern __shared__ __align__(16) uint32_t smem[];
     static_assert(CI % 16 == 0 && CO % 16 == 0, "k steps of 16 and pairs of n tiles");
     constexpr int IW = in_words<CI>(), WW = w_words<CI>(), CW = CI / 2, KW = 9 * CI / 2;
+    constexpr int TW = tile_words<CI>(), CH = CW / 4;  // 16-byte chunks per pixel
+    static_assert(CW % 4 == 0 && IW % 4 == 0, "16-byte pixel rows");
     uint32_t* s_w = smem;
-    uint32_t* s_in = smem + CO * WW;
     for (int i = threadIdx.x; i < CO * KW; i += CONV_THREADS) s_w[(i / KW) * WW + (i % KW)] = w[i];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
     const int tiles_y = H / TROWS, tiles_x = W / TCOLS;
     const long long ntiles = (long long)B * tiles_y * tiles_x;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the input of a tile (with its periodic halo) into buffer b, asynchronously
+    auto load_tile = [&](long long tile, int b) {
         const int tx = (int)(tile % tiles_x);
         const long long r = tile / tiles_x;
         const int ty = (int)(r % tiles_y), n = (int)(r / tiles_y);
         const int y0 = ty * TROWS, x0 = tx * TCOLS;
-        __syncthreads();  // weights stored / previous tile's reads finished
-        for (int i = threadIdx.x; i < (TROWS + 2) * (TCOLS + 2) * CW; i += CONV_THREADS) {
-            const int c = i % CW, p = i / CW, col = p % (TCOLS + 2), row = p / (TCOLS + 2);
+        uint32_t* dst = smem + CO * WW + b * TW;
+        for (int i = threadIdx.x; i < (TROWS + 2) * (TCOLS + 2) * CH; i += CONV_THREADS) {
+            const int c = i % CH, p = i / CH, col = p % (TCOLS + 2), row = p / (TCOLS + 2);
             const int yy = wrap(y0 - 1 + row, H), xx = wrap(x0 - 1 + col, W);
-            s_in[p * IW + c] = x[(((long long)n * H + yy) * W + xx) * CW + c];
+            cp_async16(dst + p * IW + 4 * c, x + (((long long)n * H + yy) * W + xx) * CW + 4 * c);
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    if (blockIdx.x < ntiles) load_tile(blockIdx.x, 0);
+    int buf = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        const int tx = (int)(tile % tiles_x);
+        const long long r = tile / tiles_x;
+        const int ty = (int)(r % tiles_y), n = (int)(r / tiles_y);
+        const int y0 = ty * TROWS, x0 = tx * TCOLS;
+        // the other buffer was last read in the previous iteration, which every
+        // thread has finished (barrier at its end): start the next tile's copy
+        if (tile + gridDim.x < ntiles) {
+            load_tile(tile + gridDim.x, buf ^ 1);
+            cp_async_wait<1>();  // this tile's copy (all but the newest group)
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // this tile's input (and, the first time, the weights) visible
+        const uint32_t* s_in = smem + CO * WW + buf * TW;
 
         float acc[2][CO / 8][4];
 #pragma unroll
@@ -168,6 +202,7 @@ __global__ void __launch_bounds__(CONV_THREADS)
                 }
             }
         }
+        __syncthreads();  // every warp is done with buffer `buf` before it is refilled
     }
 }
 
