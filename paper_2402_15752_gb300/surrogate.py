@@ -530,10 +530,39 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
     }
 
 
+def conv_bench(B=16, H=256, W=256, launches=20):
+    """Time the 48 -> 48 ReLU convolution alone (CUDA events); returns
+    (ms per launch, TFLOP/s)."""
+    import torch
+    L = nn_lib()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn((B, H, W, 48), generator=g, device=dev).to(torch.bfloat16)
+    w = (0.05 * torch.randn((48, 9, 48), generator=g, device=dev)).to(torch.bfloat16)
+    b = torch.zeros(48, dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run():
+        _ck(L.lbm_nn_conv3x3(_p(x), 48, _p(w), _p(b), 48, RELU, None, None, _p(y), B, H, W, s), "conv")
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(launches):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / launches
+    return ms, 2.0 * B * H * W * 9 * 48 * 48 / ms / 1e9
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser(description="train or evaluate the surrogate network")
-    ap.add_argument("command", choices=["train", "evaluate"])
+    ap.add_argument("command", choices=["train", "evaluate", "conv-bench"])
     ap.add_argument("--model", default=None, help="evaluate: a saved model (.npz)")
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--hops", type=int, default=8)
@@ -546,6 +575,10 @@ def main():
     ap.add_argument("--out", default="surrogate.npz")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
+    if args.command == "conv-bench":
+        ms, tf = conv_bench()
+        print("conv 48->48, batch 16 of 256 x 256: %.3f ms, %.1f TFLOP/s" % (ms, tf))
+        return
     if args.command == "evaluate":
         sur = Surrogate.load(args.model, dev)
         print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops)))
