@@ -566,6 +566,7 @@ def main():
     ap.add_argument("--model", default=None, help="evaluate: a saved model (.npz)")
     ap.add_argument("--eval-cases", type=int, default=64)
     ap.add_argument("--hops", type=int, default=8)
+    ap.add_argument("--warm", type=int, default=64, help="solver steps before the first snapshot")
     ap.add_argument("--trajectories", type=int, default=2000)
     ap.add_argument("--snapshots", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=6)
@@ -581,10 +582,11 @@ def main():
         return
     if args.command == "evaluate":
         sur = Surrogate.load(args.model, dev)
-        print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops)))
+        print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops,
+                                  warm=args.warm)))
         return
     t0 = time.perf_counter()
-    data = generate(droplet_cases(args.trajectories, 0, args.side), args.snapshots, dev)
+    data = generate(droplet_cases(args.trajectories, 0, args.side), args.snapshots, dev, warm=args.warm)
     torch.cuda.synchronize()
     print("data: %d trajectories x %d snapshots in %.1f s" % (args.trajectories, args.snapshots,
                                                              time.perf_counter() - t0), flush=True)
@@ -597,7 +599,8 @@ def main():
                       "seconds": time.perf_counter() - t0}), flush=True)
     del data
     torch.cuda.empty_cache()
-    print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops)))
+    print(json.dumps(evaluate(sur, droplet_cases(args.eval_cases, 7, args.side), hops=args.hops,
+                              warm=args.warm)))
 
 
 if __name__ == "__main__":
