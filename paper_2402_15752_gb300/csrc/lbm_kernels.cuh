@@ -123,6 +123,27 @@ __device__ __forceinline__ T from_r(R v) {
     else return T(v);
 }
 
+// 16-bit storage pairs two populations pulled from the same upstream node in
+// one 32-bit word: (f_i, g_i) for each D2Q9 direction i and (h1_i, h2_i) for
+// each scalar direction, so that a warp's load is 128 contiguous bytes as in
+// FP32.  lo16 / hi16 give the low / high value of a word in FP32.
+template <typename T>
+__device__ __forceinline__ float lo16(uint32_t w) {
+    if constexpr (std::is_same<T, __half>::value) return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    else return __uint_as_float(w << 16);
+}
+template <typename T>
+__device__ __forceinline__ float hi16(uint32_t w) {
+    if constexpr (std::is_same<T, __half>::value) return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    else return __uint_as_float(w & 0xffff0000u);
+}
+__device__ __forceinline__ unsigned short bits16(__half v) { return __half_as_ushort(v); }
+__device__ __forceinline__ unsigned short bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+template <typename T>
+__device__ __forceinline__ uint32_t pack16(T lo, T hi) {
+    return (uint32_t)bits16(lo) | ((uint32_t)bits16(hi) << 16);
+}
+
 // IEEE half storage keeps g_i * 2^10: the flow populations are of the order of
 // the pressure (1e-6 .. 1e-2 in lattice units), much of which lies below half's
 // smallest normal number (6.1e-5), while |g_i| 2^10 stays far below its largest
@@ -216,9 +237,39 @@ __device__ __forceinline__ long long pull_off(const Geometry& g, int x, int y, i
     if (oy) sy = sy < 0 ? sy + g.ny : sy - g.ny;
     return node_off<NQ>(g, sx, sy) + (plane0 + i) * 32;
 }
+// Element offset of population plane q (f: 0-8, g: 9-17, h1: 18.., h2: 18+QS..)
+// of node (x, y).  FP32/FP64: plane q of the node's 32-node block.  16-bit: the
+// node's word j of the block (j = i for f_i, g_i; 9 + i for h1_i, h2_i), low
+// half for f and h1, high half for g and h2.
+template <typename T, int NQ>
+__device__ __forceinline__ long long pop_off(const Geometry& g, int x, int y, int q) {
+    if constexpr (IsHalf<T>::value) {
+        constexpr int QS = (NQ - 18) / 2;
+        const int j = q < 9 ? q : (q < 18 ? q - 9 : (q < 18 + QS ? q - 9 : q - 9 - QS));
+        const int hi = (q >= 9 && q < 18) || q >= 18 + QS;
+        return 2 * (node_off<NQ / 2>(g, x, y) + j * 32) + hi;
+    } else {
+        return node_off<NQ>(g, x, y) + q * 32;
+    }
+}
+// pull_off in element units of a population buffer of storage type T
+template <typename T, int NQ>
+__device__ __forceinline__ long long pop_pull_off(const Geometry& g, int x, int y, int plane0, int i) {
+    if constexpr (IsHalf<T>::value) {
+        int sx = x - cx(i), sy = y - cy(i);
+        const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+        if ((ox && g.wall_x) || (oy && g.wall_y)) return pop_off<T, NQ>(g, x, y, plane0 + opp(i));
+        if (ox) sx = sx < 0 ? sx + g.nx : sx - g.nx;
+        if (oy) sy = sy < 0 ? sy + g.ny : sy - g.ny;
+        return pop_off<T, NQ>(g, sx, sy, plane0 + i);
+    } else {
+        return pull_off<NQ>(g, x, y, plane0, i);
+    }
+}
 template <int NQ, typename T, typename R, bool CG = false>
 __device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry& g, int x, int y,
                                       int plane0, int i) {
+    if constexpr (IsHalf<T>::value) return to_r<R>(ld<CG>(src + pop_pull_off<T, NQ>(g, x, y, plane0, i)));
     int sx = x - cx(i), sy = y - cy(i);
     const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
     if ((ox && g.wall_x) || (oy && g.wall_y))
@@ -306,10 +357,24 @@ constexpr float FIX_EPS = 4.656612873077392578125e-10f;  // 2^-31
 constexpr double FIX_EPS_D = 4.656612873077392578125e-10;
 
 // Pulled f, h1, h2 of one node (f in its storage form).
-template <typename T, typename R, int QS>
+template <typename T, typename R, int QS, bool PAIRED = IsHalf<T>::value>
 struct NodeFH {
     typename PhaseFix<T>::S f[9];
     R h1[QS], h2[QS];
+    __device__ __forceinline__ typename PhaseFix<T>::S F(int i) const { return f[i]; }
+    __device__ __forceinline__ R H1(int i) const { return h1[i]; }
+    __device__ __forceinline__ R H2(int i) const { return h2[i]; }
+};
+// 16-bit storage: the pulled words as loaded, converted where used; the g
+// halves ride along with f and are used one row later
+template <typename T, typename R, int QS>
+struct NodeFH<T, R, QS, true> {
+    uint32_t fg[9];   // (f_i - w_i / 2, g_i stored form)
+    uint32_t hh[QS];  // (h1_i, h2_i)
+    __device__ __forceinline__ float F(int i) const { return lo16<T>(fg[i]) + 0.5f * w9<float>(i); }
+    __device__ __forceinline__ float G(int i) const { return hi16<T>(fg[i]); }
+    __device__ __forceinline__ float H1(int i) const { return lo16<T>(hh[i]); }
+    __device__ __forceinline__ float H2(int i) const { return hi16<T>(hh[i]); }
 };
 
 // Fast pull: interior node at element offset `nd`, upstream offsets `doff`.
@@ -317,6 +382,15 @@ struct NodeFH {
 template <int QS, typename T, typename R, bool CG = false, bool ONE = false>
 __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long long nd,
                                              const int (&doff)[9], NodeFH<T, R, QS>& P) {
+    if constexpr (IsHalf<T>::value) {
+        // nd, doff in 32-bit words
+        const uint32_t* sw = reinterpret_cast<const uint32_t*>(src);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P.fg[i] = ld<CG>(sw + nd + doff[i] + i * 32);
+#pragma unroll
+        for (int i = 0; i < QS; ++i) P.hh[i] = ld<CG>(sw + nd + doff[i] + (9 + i) * 32);
+        return;
+    } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) P.f[i] = load_f<T, CG>(src, nd + doff[i] + i * 32, i);
 #pragma unroll
@@ -324,12 +398,23 @@ __device__ __forceinline__ void pull_fh_fast(const T* __restrict__ src, long lon
         P.h1[i] = to_r<R>(ld<CG>(src + nd + doff[i] + (18 + i) * 32));
         P.h2[i] = ONE ? R(0) : to_r<R>(ld<CG>(src + nd + doff[i] + (18 + QS + i) * 32));
     }
+    }
 }
 
 template <int QS, typename T, typename R, bool CG = false, bool ONE = false>
 __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geometry& g, int x,
                                             int y, NodeFH<T, R, QS>& P) {
     constexpr int NQ = nq_of(QS);
+    if constexpr (IsHalf<T>::value) {
+        // whole words: bounce-back takes f and g (h1 and h2) of the same
+        // opposite direction, which share a word
+        const uint32_t* sw = reinterpret_cast<const uint32_t*>(src);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P.fg[i] = ld<CG>(sw + pull_off<NQ / 2>(g, x, y, 0, i));
+#pragma unroll
+        for (int i = 0; i < QS; ++i) P.hh[i] = ld<CG>(sw + pull_off<NQ / 2>(g, x, y, 9, i));
+        return;
+    } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         if constexpr (PhaseFix<T>::on)
@@ -342,12 +427,13 @@ __device__ __forceinline__ void pull_fh_any(const T* __restrict__ src, const Geo
         P.h1[i] = pull_any<NQ, T, R, CG>(src, g, x, y, 18, i);
         P.h2[i] = ONE ? R(0) : pull_any<NQ, T, R, CG>(src, g, x, y, 18 + QS, i);
     }
+    }
 }
 
 // phi in storage form (exact integer sum for fixed point) and as a number
 template <typename T, typename R, int QS>
 __device__ __forceinline__ typename PhaseFix<T>::S phase_sum(const NodeFH<T, R, QS>& P) {
-    return ((P.f[0] + (P.f[1] + P.f[3])) + (P.f[2] + P.f[4])) + ((P.f[5] + P.f[7]) + (P.f[6] + P.f[8]));
+    return ((P.F(0) + (P.F(1) + P.F(3))) + (P.F(2) + P.F(4))) + ((P.F(5) + P.F(7)) + (P.F(6) + P.F(8)));
 }
 // phi and 1 - phi from the stored form; in fixed point each is formed as an
 // exact integer before the conversion, so phi is exact to float precision
@@ -393,8 +479,8 @@ __device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS
     R P1 = R(0), P2 = R(0);
 #pragma unroll
     for (int i = 0; i < QS; ++i) {
-        P1 += P.h1[i];
-        P2 += P.h2[i];
+        P1 += P.H1(i);
+        P2 += P.H2(i);
     }
     if constexpr (ONE) henry_split(C, phi, P1, c1, c2);  // c = sum_i h3_i
     else solve_scalars(C, phi, omp, P1, P2, c1, c2);
@@ -468,20 +554,33 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
         }
         stcs(oi, phis - sum);
     } else {
-        // 16-bit storage keeps f_i - w_i/2; the rest population takes what the
-        // stored moving populations leave of phi
-        const R off = IsHalf<T>::value ? R(0.5) : R(0);
         const R a0 = omega * phi, keep = R(1) - omega;
         R sum = R(0);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-            const T vs = store_value<T>(keep * R(f[i]) + w9<R>(i) * (a0 + cB) - off * w9<R>(i), pop_key(key, i));
-            sum += to_r<R>(vs) + off * w9<R>(i);
+            const T vs = keep * R(f[i]) + w9<R>(i) * (a0 + cB);
+            sum += vs;
             stcs(o + i * 32, vs);
         }
-        stcs(o, store_value<T>(phi - sum - off * w9<R>(0), key));
+        stcs(o, phi - sum);
     }
+}
+// The same for 16-bit storage: the stored forms f*_i - w_i / 2, rounded
+// stochastically, go to fs (they are written together with g*_i); the rest
+// population takes what the rounded moving ones leave of phi.
+template <typename T, typename R, int QS>
+__device__ __forceinline__ void collide_f16(T (&fs)[9], const NodeFH<T, R, QS>& P, R phi, R omega, R Bx,
+                                            R By, uint32_t key) {
+    const R a0 = omega * phi, keep = R(1) - omega;
+    R sum = R(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
+        fs[i] = store_value<T>(keep * P.F(i) + w9<R>(i) * (a0 + cB) - R(0.5) * w9<R>(i), pop_key(key, i));
+        sum += to_r<R>(fs[i]) + R(0.5) * w9<R>(i);
+    }
+    fs[0] = store_value<T>(phi - sum - R(0.5) * w9<R>(0), key);
 }
 
 // One tile of the fused step (FIELDS = false) or of the macroscopic-field
@@ -498,6 +597,9 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                                            void* __restrict__ out, int out_f64, int x0, int ya,
                                            int yb) {
     constexpr int NQ = nq_of(QS);
+    // 16-bit storage is addressed in 32-bit words (two populations each)
+    constexpr bool PAIRED = IsHalf<T>::value;
+    constexpr int NQL = PAIRED ? NQ / 2 : NQ;
     constexpr int W2 = W + 2;
     constexpr bool ONE = (VAR & 1) != 0;
     constexpr int GS = VAR >> 1;
@@ -520,10 +622,10 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     const bool h_inner = hraw == hx && hx >= 1 && hx <= g.nx - 2;
     const int hcol = tid == 0 ? W + 1 : 0;
 
-    // upstream offsets of an interior node (element units, relative to the node)
-    const int row = g.nxb * NQ * 32;
-    const int xm = lane == 0 ? 31 - NQ * 32 : -1;  // node x - 1
-    const int xp = lane == 31 ? NQ * 32 - 31 : 1;  // node x + 1
+    // upstream offsets of an interior node (element or word units, relative to the node)
+    const int row = g.nxb * NQL * 32;
+    const int xm = lane == 0 ? 31 - NQL * 32 : -1;  // node x - 1
+    const int xp = lane == 31 ? NQL * 32 - 31 : 1;  // node x + 1
     int doff[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) doff[i] = -cy(i) * row + (cx(i) == 1 ? xm : (cx(i) == -1 ? xp : 0));
@@ -534,7 +636,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         PS phis;
         R phi, c1, c2;
         if (x_inner && ry >= 1 && ry <= g.ny - 2)
-            pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQ>(g, x, ry), doff, P);
+            pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, x, ry), doff, P);
         else
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
         zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
@@ -546,7 +648,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             PS hs;
             R a, b, c;
             if (h_inner && ry >= 1 && ry <= g.ny - 2)
-                pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQ>(g, hx, ry), doff, hp);
+                pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, hx, ry), doff, hp);
             else
                 pull_fh_any<QS, T, R, CG, ONE>(src, g, hx, ry, hp);
             zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
@@ -562,11 +664,15 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 
     for (int y = ya; y < yb; ++y) {
         const bool inner = x_inner && y >= 1 && y <= g.ny - 2;
-        const long long nd = node_off<NQ>(g, x, y);
+        const long long nd = node_off<NQL>(g, x, y);
         // ---- a. loads of row y: g (pulled) and the previous-step macros ----
         R gp[9], pv[5];
         if (col_in) {
-            if (inner) {
+            if constexpr (PAIRED) {
+                // pulled with f one row ago
+#pragma unroll
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(cur.G(i));
+            } else if (inner) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ld<CG>(src + nd + doff[i] + (9 + i) * 32)));
             } else {
@@ -693,15 +799,18 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 const R inv_norm = div_r(R(1), norm_r(dphix, dphiy) + R(1e-4));
                 const R nxv = dphix * inv_norm, nyv = dphiy * inv_norm;
                 T* o = dst + nd;
+                uint32_t* ow = reinterpret_cast<uint32_t*>(dst) + nd;  // 16-bit storage
                 // random-bit key of this node (used by 16-bit storage only)
                 const uint32_t key = IsHalf<T>::value ? mix32((uint32_t)y * 0x01000193u + (uint32_t)x) : 0u;
 
                 // ---- e1. f (Eqs. 23-25) ----
+                T fs[9];  // 16-bit storage: f*, stored with g*
                 {
                     const R sharp = C.force_f * C.four_over_W * phi * omp;
                     const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
                     const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
-                    collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By, key);
+                    if constexpr (PAIRED) collide_f16<T, R, QS>(fs, cur, phi, C.omega_f, Bx, By, key);
+                    else collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By, key);
                 }
                 // ---- e2. g (Eqs. 28-31) ----
                 {
@@ -718,7 +827,9 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
                         R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
                         if (i == 0) v -= R(3) * omega_g * p;
-                        stcs(o + (9 + i) * 32, store_value<T>(g_stored<T>(v), pop_key(key, 9 + i)));
+                        const T gv = store_value<T>(g_stored<T>(v), pop_key(key, 9 + i));
+                        if constexpr (PAIRED) stcs(ow + i * 32, pack16<T>(fs[i], gv));
+                        else stcs(o + (9 + i) * 32, gv);
                     }
                 }
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
@@ -729,7 +840,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     // what the moving ones leave of c = sum_i h3_i (exact conservation)
                     R P1 = R(0), s1 = R(0);
 #pragma unroll
-                    for (int i = 0; i < QS; ++i) P1 += cur.h1[i];
+                    for (int i = 0; i < QS; ++i) P1 += cur.H1(i);
                     const R ph = phi < R(0) ? R(0) : (phi > R(1) ? R(1) : phi);
                     const R omp_c = R(1) - ph;
                     const R w3 = div_r(R(1), R(3) * (C.KD1 * ph + C.D2 * omp_c) + R(0.5));
@@ -742,7 +853,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     for (int i = 1; i < QS; ++i) {
                         const R w = wq<R, QS>(i);
                         const R cB = (cx(i) ? R(cx(i)) * B3x : R(0)) + (cy(i) ? R(cy(i)) * B3y : R(0));
-                        const T v = store_value<T>(k3 * cur.h1[i] + w * (a3 + cB), pop_key(key, 18 + i));
+                        const T v = store_value<T>(k3 * cur.H1(i) + w * (a3 + cB), pop_key(key, 18 + i));
                         s1 += to_r<R>(v);
                         stcs(o + (18 + i) * 32, v);
                     }
@@ -753,8 +864,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         R m1x = R(0), m1y = R(0), m2x = R(0), m2y = R(0);
 #pragma unroll
                         for (int i = 1; i < QS; ++i) {
-                            if (cx(i)) { m1x += R(cx(i)) * cur.h1[i]; m2x += R(cx(i)) * cur.h2[i]; }
-                            if (cy(i)) { m1y += R(cy(i)) * cur.h1[i]; m2y += R(cy(i)) * cur.h2[i]; }
+                            if (cx(i)) { m1x += R(cx(i)) * cur.H1(i); m2x += R(cx(i)) * cur.H2(i); }
+                            if (cy(i)) { m1y += R(cy(i)) * cur.H1(i); m2y += R(cy(i)) * cur.H2(i); }
                         }
                         const R s1n = C.D1 * C.four_over_W * omp * c1, s2n = C.D2 * C.four_over_W * phi * c2;
                         const R k1 = R(3) * C.omega_h1, k2 = R(3) * C.omega_h2;  // 1 / (tau cs^2)
@@ -778,26 +889,36 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     R P1 = R(0), P2 = R(0), s1 = R(0), s2 = R(0);
 #pragma unroll
                     for (int i = 0; i < QS; ++i) {
-                        P1 += cur.h1[i];
-                        P2 += cur.h2[i];
+                        P1 += cur.H1(i);
+                        P2 += cur.H2(i);
                     }
 #pragma unroll
                     for (int i = 1; i < QS; ++i) {
                         const R w = wq<R, QS>(i);
                         const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
                         const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
-                        const T v1 = store_value<T>(k1 * cur.h1[i] + w * (a1 + c1B), pop_key(key, 18 + i));
-                        const T v2 = store_value<T>(k2 * cur.h2[i] + w * (a2 + c2B), pop_key(key, 18 + QS + i));
+                        const T v1 = store_value<T>(k1 * cur.H1(i) + w * (a1 + c1B), pop_key(key, 18 + i));
+                        const T v2 = store_value<T>(k2 * cur.H2(i) + w * (a2 + c2B), pop_key(key, 18 + QS + i));
                         s1 += to_r<R>(v1);
                         s2 += to_r<R>(v2);
-                        stcs(o + (18 + i) * 32, v1);
-                        stcs(o + (18 + QS + i) * 32, v2);
+                        if constexpr (PAIRED) {
+                            stcs(ow + (9 + i) * 32, pack16<T>(v1, v2));
+                        } else {
+                            stcs(o + (18 + i) * 32, v1);
+                            stcs(o + (18 + QS + i) * 32, v2);
+                        }
                     }
                     // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
                     // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
                     // without c1 they cannot inherit its rounding, and P1 + P2 is kept
-                    stcs(o + 18 * 32, store_value<T>((P1 + (S1 - Ht)) - s1, pop_key(key, 18)));
-                    stcs(o + (18 + QS) * 32, store_value<T>((P2 - (S1 - Ht)) - s2, pop_key(key, 18 + QS)));
+                    const T r1 = store_value<T>((P1 + (S1 - Ht)) - s1, pop_key(key, 18));
+                    const T r2 = store_value<T>((P2 - (S1 - Ht)) - s2, pop_key(key, 18 + QS));
+                    if constexpr (PAIRED) {
+                        stcs(ow + 9 * 32, pack16<T>(r1, r2));
+                    } else {
+                        stcs(o + 18 * 32, r1);
+                        stcs(o + (18 + QS) * 32, r2);
+                    }
                 }
             }
         }
@@ -838,7 +959,7 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
     // populations are written pre-streamed: direction i of node (x, y) goes where
     // the next step pulls it from
     auto put = [&](int plane0, int i, double v) {
-        pop[pull_off<NQ>(g, x, y, plane0, i)] = from_r<T>(v);
+        pop[pop_pull_off<T, NQ>(g, x, y, plane0, i)] = from_r<T>(v);
     };
     auto cu_of = [&](int i) { return double(cx(i)) * ux + double(cy(i)) * uy; };
     for (int i = 0; i < 9; ++i) {
@@ -867,7 +988,7 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
             const double w = w9<double>(i);
             const T v = from_r<T>(w * phi * (1.0 + 3.0 * cu_of(i)) - 0.5 * w);
             sum += double(to_r<float>(v));
-            pop[pull_off<NQ>(g, x, y, 0, i)] = v;
+            pop[pop_pull_off<T, NQ>(g, x, y, 0, i)] = v;
         }
         put(0, 0, (phi - 0.5) - sum);
     } else {
@@ -916,7 +1037,7 @@ __global__ void __launch_bounds__(RED_THREADS)
             for (int i = 0; i < 9; ++i) s += load_f<T>(pop, pull_off<NQ>(g, x, y, 0, i), i);
             ai += s;
         } else {
-            for (int i = 0; i < 9; ++i) a += double(load_f<T>(pop, pull_off<NQ>(g, x, y, 0, i), i));
+            for (int i = 0; i < 9; ++i) a += double(load_f<T>(pop, pop_pull_off<T, NQ>(g, x, y, 0, i), i));
         }
         double c = 0.0;
         for (int i = 0; i < QS; ++i)

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(NA_THREADS)
             for (int i = 0; i < 9; ++i) s += lbm::load_f<T>(pop, lbm::pull_off<NQ>(g, x, y, 0, i), i);
             ai += s;
         } else {
-            for (int i = 0; i < 9; ++i) a += double(lbm::load_f<T>(pop, lbm::pull_off<NQ>(g, x, y, 0, i), i));
+            for (int i = 0; i < 9; ++i) a += double(lbm::load_f<T>(pop, lbm::pop_pull_off<T, NQ>(g, x, y, 0, i), i));
         }
         for (int i = 0; i < QS; ++i)
             b += lbm::pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
