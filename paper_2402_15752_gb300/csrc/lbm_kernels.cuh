@@ -168,9 +168,15 @@ __device__ __forceinline__ R g_stored(R v) {
 // probability equal to its distance from the lower one, in ulps.  The stored
 // value is then exact on average, and increments smaller than half an ulp -- the
 // slow diffusive and sharpening updates of the populations -- are not rounded
-// away every step as they are under round-to-nearest.  The random bits are a hash
-// (the 32-bit finalizer of MurmurHash3) of the value's bits and a key per node and
-// population, so a run is deterministic and a checkpoint restarts bit-identically.
+// away every step as they are under round-to-nearest.
+//
+// Random bits: a seed per node and step (the 32-bit finalizer of MurmurHash3
+// applied to the node's coordinates and the bits of its new macros) is xored
+// with the bits of the value to round and multiplied by an odd constant per
+// population (a multiplicative hash, Knuth's Fibonacci hashing); the top bits
+// are used.  For a uniform seed the product is uniform whatever the value, so
+// the rounding stays unbiased, and a run is deterministic: graph and plain
+// launches, and a restart from a checkpoint, give the same bits.
 __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -179,32 +185,39 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
+// random word for population q (0 .. 35) of a node with seed h, value bits vb
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, uint32_t vb, int q) {
+    return (h ^ vb) * (0x9e3779b9u + (uint32_t)q * 0x3c6ef372u);
+}
+// v rounded to T with the random word r: a uniform fraction of one ulp of the
+// 16-bit grid at |v| is added to |v| and the sum truncated.
 template <typename T>
-__device__ __forceinline__ T round16_stochastic(float v, uint32_t key) {
-    const uint32_t r = mix32(__float_as_uint(v) ^ key);
+__device__ __forceinline__ T round16_stochastic(float v, uint32_t r) {
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        // bfloat16 is the upper half of the float's bits: add 16 random low bits
-        // and truncate (the carry moves into the exponent where it should)
-        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16));
+        // bfloat16 is the upper half of the float's encoding: add 16 random bits
+        // to the low half and truncate (a carry moves into the exponent, where
+        // the grid spacing doubles as the encoding's does)
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
     } else {
-        // half: one ulp at |v| is 2^(e - 10), e = max(exponent of v, -14);
-        // add a uniform fraction of it to |v| and truncate towards zero
+        // half: one ulp at |v| is 2^(e - 10), e = max(exponent of |v|, -14) (the
+        // spacing stays 2^-24 below 2^-14, so the sum is formed in float
+        // arithmetic); the fraction is the top 24 bits of r
         const float a = fabsf(v);
-        const int e = max((int)(__float_as_uint(a) >> 23) - 127, -14);
-        const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
-        return __float2half_rz(copysignf(fmaf(float(r >> 8) * 0x1p-24f, ulp, a), v));
+        const float m = fmaxf(a, 0x1p-14f);
+        const float ulp24 = __uint_as_float((__float_as_uint(m) & 0x7f800000u) - (34u << 23));  // 2^(e-34)
+        return __float2half_rz(copysignf(fmaf(float(r >> 8), ulp24, a), v));
     }
 }
 // A value of the arithmetic type R as stored in T: 16-bit storage rounds
-// stochastically with the given key, FP32/FP64 storage converts exactly.
+// stochastically (node seed h, population q), FP32/FP64 storage converts exactly.
 template <typename T, typename R>
-__device__ __forceinline__ T store_value(R v, uint32_t key) {
-    if constexpr (IsHalf<T>::value) return round16_stochastic<T>(float(v), key);
-    else return T(v);
-}
-// key of population plane q of the node with linear index k
-__device__ __forceinline__ uint32_t pop_key(uint32_t node_key, int q) {
-    return node_key + (uint32_t)q * 0x9e3779b9u;
+__device__ __forceinline__ T store_value(R v, uint32_t h, int q) {
+    if constexpr (IsHalf<T>::value) {
+        const float f = float(v);
+        return round16_stochastic<T>(f, sr_bits(h, __float_as_uint(f), q));
+    } else {
+        return T(v);
+    }
 }
 
 // Node coordinate seen by a stencil: periodic wrap, or the mirror ghost of
@@ -577,10 +590,10 @@ __device__ __forceinline__ void collide_f16(T (&fs)[9], const NodeFH<T, R, QS>& 
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-        fs[i] = store_value<T>(keep * P.F(i) + w9<R>(i) * (a0 + cB) - R(0.5) * w9<R>(i), pop_key(key, i));
+        fs[i] = store_value<T>(keep * P.F(i) + w9<R>(i) * (a0 + cB) - R(0.5) * w9<R>(i), key, i);
         sum += to_r<R>(fs[i]) + R(0.5) * w9<R>(i);
     }
-    fs[0] = store_value<T>(phi - sum - R(0.5) * w9<R>(0), key);
+    fs[0] = store_value<T>(phi - sum - R(0.5) * w9<R>(0), key, 0);
 }
 
 // One tile of the fused step (FIELDS = false) or of the macroscopic-field
@@ -793,15 +806,22 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     pp[128] = ONE ? R(0) : c2;
                 }
                 // non-finite values, or phi outside the fixed-point range
-                if (!finite5(phi, ux, uy, c1, c2) || !(phi > R(-1.5) && phi < R(1.5))) atomicOr(flag, 1u);
+                // (16-bit storage also checks p: rounding a NaN population can lose
+                // it, and g_0 reaches no other macro)
+                if (!finite5(phi, ux, uy, c1, c2) || !(phi > R(-1.5) && phi < R(1.5)) ||
+                    (IsHalf<T>::value && !isfinite(p)))
+                    atomicOr(flag, 1u);
 
                 // unit normal (Eq. 1), regularised
                 const R inv_norm = div_r(R(1), norm_r(dphix, dphiy) + R(1e-4));
                 const R nxv = dphix * inv_norm, nyv = dphiy * inv_norm;
                 T* o = dst + nd;
                 uint32_t* ow = reinterpret_cast<uint32_t*>(dst) + nd;  // 16-bit storage
-                // random-bit key of this node (used by 16-bit storage only)
-                const uint32_t key = IsHalf<T>::value ? mix32((uint32_t)y * 0x01000193u + (uint32_t)x) : 0u;
+                // stochastic-rounding seed of this node and step (16-bit storage only)
+                const uint32_t key =
+                    IsHalf<T>::value ? mix32(((uint32_t)y * 0x01000193u + (uint32_t)x) ^ __float_as_uint(float(p)) ^
+                                             (__float_as_uint(float(ux)) * 0x2545f491u))
+                                     : 0u;
 
                 // ---- e1. f (Eqs. 23-25) ----
                 T fs[9];  // 16-bit storage: f*, stored with g*
@@ -827,7 +847,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
                         R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
                         if (i == 0) v -= R(3) * omega_g * p;
-                        const T gv = store_value<T>(g_stored<T>(v), pop_key(key, 9 + i));
+                        const T gv = store_value<T>(g_stored<T>(v), key, 9 + i);
                         if constexpr (PAIRED) stcs(ow + i * 32, pack16<T>(fs[i], gv));
                         else stcs(o + (9 + i) * 32, gv);
                     }
@@ -853,11 +873,11 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     for (int i = 1; i < QS; ++i) {
                         const R w = wq<R, QS>(i);
                         const R cB = (cx(i) ? R(cx(i)) * B3x : R(0)) + (cy(i) ? R(cy(i)) * B3y : R(0));
-                        const T v = store_value<T>(k3 * cur.H1(i) + w * (a3 + cB), pop_key(key, 18 + i));
+                        const T v = store_value<T>(k3 * cur.H1(i) + w * (a3 + cB), key, 18 + i);
                         s1 += to_r<R>(v);
                         stcs(o + (18 + i) * 32, v);
                     }
-                    stcs(o + 18 * 32, store_value<T>(P1 - s1, pop_key(key, 18)));
+                    stcs(o + 18 * 32, store_value<T>(P1 - s1, key, 18));
                 } else {
                     if constexpr (GS >= 1) {
                         // local grad c1, grad c2 (Eq. 39) from the first moments of h1, h2
@@ -897,8 +917,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         const R w = wq<R, QS>(i);
                         const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
                         const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
-                        const T v1 = store_value<T>(k1 * cur.H1(i) + w * (a1 + c1B), pop_key(key, 18 + i));
-                        const T v2 = store_value<T>(k2 * cur.H2(i) + w * (a2 + c2B), pop_key(key, 18 + QS + i));
+                        const T v1 = store_value<T>(k1 * cur.H1(i) + w * (a1 + c1B), key, 18 + i);
+                        const T v2 = store_value<T>(k2 * cur.H2(i) + w * (a2 + c2B), key, 18 + QS + i);
                         s1 += to_r<R>(v1);
                         s2 += to_r<R>(v2);
                         if constexpr (PAIRED) {
@@ -911,8 +931,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
                     // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
                     // without c1 they cannot inherit its rounding, and P1 + P2 is kept
-                    const T r1 = store_value<T>((P1 + (S1 - Ht)) - s1, pop_key(key, 18));
-                    const T r2 = store_value<T>((P2 - (S1 - Ht)) - s2, pop_key(key, 18 + QS));
+                    const T r1 = store_value<T>((P1 + (S1 - Ht)) - s1, key, 18);
+                    const T r2 = store_value<T>((P2 - (S1 - Ht)) - s2, key, 18 + QS);
                     if constexpr (PAIRED) {
                         stcs(ow + 9 * 32, pack16<T>(r1, r2));
                     } else {

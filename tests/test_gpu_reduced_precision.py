@@ -84,8 +84,8 @@ def _erfc_errors(f, p, steps):
 # cases; its error grows with the steps.
 PLANAR_TOL = {
     "fp32": dict(phi=1.5e-4, c1=1.5e-4, c2=1.5e-4, rho=1.5e-4, mu=1.5e-4, erfc=3e-3),
-    "bf16": dict(phi=0.25, c1=0.15, c2=0.05, rho=1e-6, mu=1e-6, erfc=0.1),
-    "fp16": dict(phi=0.06, c1=0.025, c2=0.008, rho=1e-6, mu=1e-6, erfc=0.02),
+    "bf16": dict(phi=0.16, c1=0.16, c2=0.05, rho=1e-6, mu=1e-6, erfc=0.03),
+    "fp16": dict(phi=0.018, c1=0.018, c2=6.5e-3, rho=1e-6, mu=1e-6, erfc=6e-3),
 }
 
 
@@ -124,13 +124,13 @@ def _bubble_small():
 
 CASE_TOL = {  # about twice the measured error, relative to each field's natural scale
     "droplet64": {
-        "bf16": dict(phi=0.05, ux=1.2, uy=1.2, p=0.4, c1=0.025, c2=0.01, rho=1e-6, mu=1e-6),
-        "fp16": dict(phi=8e-3, ux=0.14, uy=0.14, p=0.06, c1=4e-3, c2=1.6e-3, rho=1e-6, mu=1e-6),
+        "bf16": dict(phi=0.025, ux=0.45, uy=0.55, p=0.19, c1=0.015, c2=5.5e-3, rho=1e-6, mu=1e-6),
+        "fp16": dict(phi=2e-3, ux=0.065, uy=0.055, p=0.028, c1=1.6e-3, c2=8.5e-4, rho=1e-6, mu=1e-6),
     },
     "bubble_small": {
-        "bf16": dict(phi=0.02, ux=1.8, uy=2.7, p=0.06, c1=2.5e-4, c2=0.1, rho=0.02, mu=0.02),
-        "fp16": dict(phi=3.5e-3, ux=0.22, uy=0.26, p=5e-3, c1=2.5e-5, c2=9e-3, rho=3.5e-3,
-                     mu=3.5e-3),
+        "bf16": dict(phi=0.014, ux=1.15, uy=1.4, p=0.04, c1=2.1e-4, c2=0.06, rho=0.014, mu=0.014),
+        "fp16": dict(phi=3.2e-3, ux=0.12, uy=0.15, p=3.6e-3, c1=1.8e-5, c2=7.1e-3, rho=3.2e-3,
+                     mu=3.2e-3),
     },
 }
 _CASE_ORACLE = {}
@@ -152,7 +152,7 @@ def test_case_fields_per_storage(name, storage):
 
 
 # ------------------------------------------------------------ conservation --
-CONS_TOL = {"bf16": 5e-3, "fp16": 1e-3}
+CONS_TOL = {"bf16": 3.5e-3, "fp16": 6e-4}
 
 
 @pytest.mark.parametrize("storage", STORAGES)
@@ -160,7 +160,8 @@ def test_conserved_sums_wander_at_rounding_level(storage):
     """sum phi and sum (c1 + c2) are conserved by the method.  With 16-bit
     storage the rounding of each stored rest population changes a node's
     total; stochastic rounding makes that change zero on average, so the
-    totals wander instead of drifting (static droplet, 2000 steps)."""
+    totals wander instead of drifting (static droplet, 2000 steps): a random
+    walk of one rounding per node and step, ~ u sqrt(nodes * steps) w_0 / 2."""
     w = wl.droplet64()
     sim = run_gpu(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 0, storage)
     s0 = sim.conserved()
@@ -206,25 +207,27 @@ def test_bubble_1024x2048_fp16_against_fp32():
     print("gas centroid fp32 (%.3f, %.3f) area %.1f; fp16 (%.3f, %.3f) area %.1f"
           % (x0, y0, a0, x1, y1, a1))
     assert all(np.isfinite(v).all() for v in got.values())
-    # the bubble has risen ~45 nodes; with half storage it trails by a few
-    assert abs(x1 - x0) < 0.5 and abs(y1 - y0) < 5.0
-    assert abs(a1 - a0) / a0 < 0.02
-    assert rms["phi"] < 3e-3 and rms["c1"] < 1e-4 and rms["c2"] < 7e-3
-    assert rms["ux"] < 0.02 and rms["uy"] < 0.08 and rms["p"] < 5e-3
+    # the bubble has risen ~45 nodes; with half storage it is within a couple
+    assert abs(x1 - x0) < 0.5 and abs(y1 - y0) < 3.0
+    assert abs(a1 - a0) / a0 < 0.01
+    assert rms["phi"] < 1e-3 and rms["c1"] < 3e-5 and rms["c2"] < 2.1e-3
+    assert rms["ux"] < 0.031 and rms["uy"] < 0.035 and rms["p"] < 1.9e-3
 
 
 def test_bfloat16_storage_of_the_density_ratio_1000_bubble_is_reported_unstable():
     """bfloat16 keeps 8 significant bits.  In the gas (rho = 1e-3) the velocity
     is the flow populations' first moment divided by rho, so their rounding
-    noise (2^-8 of g ~ w_i 3p) is amplified a thousandfold and the run blows
-    up; the solver must say so rather than return garbage."""
+    noise (2^-8 of g ~ w_i 3p) is amplified a thousandfold; at the full
+    1024x2048 size the run blows up within a few thousand steps, and the solver
+    must say so rather than return garbage."""
     from paper_2402_15752_gb300.lbm import LBM_ERR_NONFINITE, LBMError
-    w = wl.bubble1024x2048(nx=96, ny=192)
+    w = wl.bubble1024x2048()
     sim = run_gpu(w.params, ("sdf", w.sdf, w.c1_tilde, w.c2_tilde), 0, "bf16")
     with pytest.raises(LBMError) as e:
-        for _ in range(20):
-            sim.step(100)
+        for k in range(50):
+            sim.step(200)
             sim.sync()
+    print("\nbubble1024x2048/bf16 non-finite reported within %d steps" % (200 * (k + 1)))
     assert e.value.code == LBM_ERR_NONFINITE
 
 
