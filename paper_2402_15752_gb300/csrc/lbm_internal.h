@@ -23,6 +23,12 @@ namespace lbm {
 constexpr int STRIP_WARPS = LBM_STRIP_WARPS;
 constexpr int STRIP_W = 32 * STRIP_WARPS;
 constexpr int STRIP_MIN_BLOCKS = LBM_STRIP_MIN_BLOCKS;  // occupancy target (register cap)
+// 16-bit storage keeps the pulled populations as packed words and fits a
+// tighter register cap without spills: more CTAs per SM
+#ifndef LBM_STRIP_MIN_BLOCKS_16
+#define LBM_STRIP_MIN_BLOCKS_16 6
+#endif
+constexpr int STRIP_MIN_BLOCKS_16 = LBM_STRIP_MIN_BLOCKS_16;
 // Blocks of the conserved-sum reduction (fixed, so the summation order is fixed).
 constexpr int RED_BLOCKS = 304;
 constexpr int RED_THREADS = 256;

@@ -949,7 +949,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 // One launch = one step (or one field evaluation) of a single lattice: CTA
 // (bx, by) owns columns bx*STRIP_W .. +STRIP_W-1 of rows by*strip_h .. +strip_h-1.
 template <typename T, typename R, int QS, bool FIELDS, int VAR = 0>
-__global__ void __launch_bounds__(STRIP_W, STRIP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STRIP_W, IsHalf<T>::value ? STRIP_MIN_BLOCKS_16 : STRIP_MIN_BLOCKS)
     strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
                  Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
                  int out_f64) {
