@@ -624,32 +624,49 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     const int x = x0 + tid;
     const bool col_in = x < g.nx;
     const int rx = col_in ? x : resolve(x, g.nx, g.wall_x);
-    const bool x_inner = col_in && x >= 1 && x <= g.nx - 2;
     // Halo columns: lane 0 (tid 0) takes the right one, x0 + W, and lane 31
-    // (tid W - 1) the left one, x0 - 1.  Each halo node then sits at the same
-    // position in its 32-node block as the lane's own node, so it reuses the
-    // lane's upstream offsets on the fast path.
+    // (tid W - 1) the left one, x0 - 1 (resolved: periodic image or wall ghost).
     const bool halo = tid == 0 || tid == W - 1;
-    const int hraw = tid == 0 ? x0 + W : x0 - 1;
-    const int hx = resolve(hraw, g.nx, g.wall_x);
-    const bool h_inner = hraw == hx && hx >= 1 && hx <= g.nx - 2;
+    const int hx = resolve(tid == 0 ? x0 + W : x0 - 1, g.nx, g.wall_x);
     const int hcol = tid == 0 ? W + 1 : 0;
 
-    // upstream offsets of an interior node (element or word units, relative to the node)
+    // Upstream offsets (element or word units, relative to the node) of the
+    // nodes of column cxn in rows 1 .. ny-2, the periodic image folded into the
+    // x neighbours; behind an x wall (bl: left, br: right) the node's own
+    // population of the opposite direction (half-way bounce-back).  The x
+    // boundary columns then take the same branch-free pull as the interior, and
+    // only rows 0 and ny-1 need pull_fh_any.
     const int row = g.nxb * NQL * 32;
-    const int xm = lane == 0 ? 31 - NQL * 32 : -1;  // node x - 1
-    const int xp = lane == 31 ? NQL * 32 - 31 : 1;  // node x + 1
-    int doff[9];
+    auto column_offsets = [&](int cxn, int (&d)[9]) {
+        const int xmn = cxn == 0 ? g.nx - 1 : cxn - 1, xpn = cxn == g.nx - 1 ? 0 : cxn + 1;
+        const int xm = ((xmn >> 5) - (cxn >> 5)) * (NQL * 32) + ((xmn & 31) - (cxn & 31));
+        const int xp = ((xpn >> 5) - (cxn >> 5)) * (NQL * 32) + ((xpn & 31) - (cxn & 31));
+        const bool bl = g.wall_x && cxn == 0, br = g.wall_x && cxn == g.nx - 1;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) doff[i] = -cy(i) * row + (cx(i) == 1 ? xm : (cx(i) == -1 ? xp : 0));
+        for (int i = 0; i < 9; ++i) {
+            const int std = -cy(i) * row + (cx(i) == 1 ? xm : (cx(i) == -1 ? xp : 0));
+            const bool bb = (cx(i) == 1 && bl) || (cx(i) == -1 && br);
+            d[i] = bb ? (opp(i) - i) * 32 : std;
+        }
+    };
+    int doff[9];
+    column_offsets(rx, doff);
+    __shared__ int s_hoff[2][9];  // the halo nodes' offsets, read by their own thread only
+    if (halo) {
+        int hd[9];
+        column_offsets(hx, hd);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s_hoff[tid == 0 ? 0 : 1][i] = hd[i];
+    }
 
     // zeroth moments of row yy into ring slot yy & 3; the pulled pops go to P
     auto moments_row = [&](int yy, NodeFH<T, R, QS>& P) {
         const int ry = resolve(yy, g.ny, g.wall_y);
+        const bool y_in = ry >= 1 && ry <= g.ny - 2;
         PS phis;
         R phi, c1, c2;
-        if (x_inner && ry >= 1 && ry <= g.ny - 2)
-            pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, x, ry), doff, P);
+        if (y_in)
+            pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, rx, ry), doff, P);
         else
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
         zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
@@ -660,8 +677,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             NodeFH<T, R, QS> hp;
             PS hs;
             R a, b, c;
-            if (h_inner && ry >= 1 && ry <= g.ny - 2)
-                pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, hx, ry), doff, hp);
+            if (y_in)
+                pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, hx, ry), s_hoff[tid == 0 ? 0 : 1], hp);
             else
                 pull_fh_any<QS, T, R, CG, ONE>(src, g, hx, ry, hp);
             zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
@@ -676,7 +693,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     moments_row(ya, cur);
 
     for (int y = ya; y < yb; ++y) {
-        const bool inner = x_inner && y >= 1 && y <= g.ny - 2;
+        const bool inner = y >= 1 && y <= g.ny - 2;
         const long long nd = node_off<NQL>(g, x, y);
         // ---- a. loads of row y: g (pulled) and the previous-step macros ----
         R gp[9], pv[5];
