@@ -18,17 +18,21 @@ namespace lbm {
 #define LBM_STRIP_WARPS 4
 #endif
 #ifndef LBM_STRIP_MIN_BLOCKS
-#define LBM_STRIP_MIN_BLOCKS 5
+#define LBM_STRIP_MIN_BLOCKS 6
 #endif
 constexpr int STRIP_WARPS = LBM_STRIP_WARPS;
 constexpr int STRIP_W = 32 * STRIP_WARPS;
 constexpr int STRIP_MIN_BLOCKS = LBM_STRIP_MIN_BLOCKS;  // occupancy target (register cap)
-// 16-bit storage keeps the pulled populations as packed words and fits a
-// tighter register cap without spills: more CTAs per SM
+// (6 CTAs = 24 warps per SM, 80 registers; FP32 fits it because the pulled
+// populations of the look-ahead row wait in shared memory.)  16-bit storage
+// has its own cap, measured separately.
 #ifndef LBM_STRIP_MIN_BLOCKS_16
 #define LBM_STRIP_MIN_BLOCKS_16 6
 #endif
 constexpr int STRIP_MIN_BLOCKS_16 = LBM_STRIP_MIN_BLOCKS_16;
+// FP64 arithmetic: 3 CTAs per SM (168 registers) keep it free of spills; its
+// speed is set by the FP64 pipe, not by memory
+constexpr int STRIP_MIN_BLOCKS_64 = 3;
 // Blocks of the conserved-sum reduction (fixed, so the summation order is fixed).
 constexpr int RED_BLOCKS = 304;
 constexpr int RED_THREADS = 256;

@@ -370,6 +370,10 @@ constexpr float FIX_EPS = 4.656612873077392578125e-10f;  // 2^-31
 constexpr double FIX_EPS_D = 4.656612873077392578125e-10;
 
 // Pulled f, h1, h2 of one node (f in its storage form).
+__device__ __forceinline__ uint32_t word_of(int v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t word_of(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ void word_to(uint32_t w, int& v) { v = (int)w; }
+__device__ __forceinline__ void word_to(uint32_t w, float& v) { v = __uint_as_float(w); }
 template <typename T, typename R, int QS, bool PAIRED = IsHalf<T>::value>
 struct NodeFH {
     typename PhaseFix<T>::S f[9];
@@ -377,6 +381,27 @@ struct NodeFH {
     __device__ __forceinline__ typename PhaseFix<T>::S F(int i) const { return f[i]; }
     __device__ __forceinline__ R H1(int i) const { return h1[i]; }
     __device__ __forceinline__ R H2(int i) const { return h2[i]; }
+    // 32-bit words per node, and their copy to / from word k * stride of p
+    // (4-byte arithmetic types only)
+    static constexpr int NW = 9 + 2 * QS;
+    __device__ __forceinline__ void save(uint32_t* p, int stride) const {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p[i * stride] = word_of(f[i]);
+#pragma unroll
+        for (int i = 0; i < QS; ++i) {
+            p[(9 + i) * stride] = word_of(h1[i]);
+            p[(9 + QS + i) * stride] = word_of(h2[i]);
+        }
+    }
+    __device__ __forceinline__ void load(const uint32_t* p, int stride) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) word_to(p[i * stride], f[i]);
+#pragma unroll
+        for (int i = 0; i < QS; ++i) {
+            word_to(p[(9 + i) * stride], h1[i]);
+            word_to(p[(9 + QS + i) * stride], h2[i]);
+        }
+    }
 };
 // 16-bit storage: the pulled words as loaded, converted where used; the g
 // halves ride along with f and are used one row later
@@ -388,6 +413,19 @@ struct NodeFH<T, R, QS, true> {
     __device__ __forceinline__ float G(int i) const { return hi16<T>(fg[i]); }
     __device__ __forceinline__ float H1(int i) const { return lo16<T>(hh[i]); }
     __device__ __forceinline__ float H2(int i) const { return hi16<T>(hh[i]); }
+    static constexpr int NW = 9 + QS;
+    __device__ __forceinline__ void save(uint32_t* p, int stride) const {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p[i * stride] = fg[i];
+#pragma unroll
+        for (int i = 0; i < QS; ++i) p[(9 + i) * stride] = hh[i];
+    }
+    __device__ __forceinline__ void load(const uint32_t* p, int stride) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fg[i] = p[i * stride];
+#pragma unroll
+        for (int i = 0; i < QS; ++i) hh[i] = p[(9 + i) * stride];
+    }
 };
 
 // Fast pull: interior node at element offset `nd`, upstream offsets `doff`.
@@ -619,6 +657,15 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     using PS = typename PhaseFix<T>::S;
     __shared__ PS s_phi[4][W2];
     __shared__ R s_c[4][2][W2];
+    // With 4-byte arithmetic the pulled f, h (and g) of a row wait for their
+    // collision, one row later, in shared memory rather than in registers: the
+    // row of look-ahead would otherwise hold them live through the next row's
+    // loads and push the kernel into spilling, and spilled values, in local
+    // memory, are evicted from L1 by the streaming loads.  Each thread reads
+    // back only its own words.
+    constexpr bool CUR_SMEM = sizeof(R) == 4;
+    constexpr int NWC = CUR_SMEM ? NodeFH<T, R, QS>::NW : 1;
+    __shared__ uint32_t s_cur[2][NWC * W];
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int x = x0 + tid;
@@ -670,6 +717,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         else
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
         zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
+        if constexpr (CUR_SMEM) P.save(&s_cur[yy & 1][tid], W);
         s_phi[yy & 3][tid + 1] = phis;
         s_c[yy & 3][0][tid + 1] = c1;
         s_c[yy & 3][1][tid + 1] = c2;
@@ -701,7 +749,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             if constexpr (PAIRED) {
                 // pulled with f one row ago
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(cur.G(i));
+                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid])));
             } else if (inner) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ld<CG>(src + nd + doff[i] + (9 + i) * 32)));
@@ -719,6 +767,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         NodeFH<T, R, QS> nxt;
         moments_row(y + 1, nxt);
         __syncthreads();
+        if constexpr (CUR_SMEM) cur.load(&s_cur[y & 1][tid], W);
 
         if (col_in) {
             // ---- c. stencils (Eqs. 41-42, D2Q9 weights) from the shared ring ----
@@ -959,14 +1008,15 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 }
             }
         }
-        cur = nxt;
+        if constexpr (!CUR_SMEM) cur = nxt;
     }
 }
 
 // One launch = one step (or one field evaluation) of a single lattice: CTA
 // (bx, by) owns columns bx*STRIP_W .. +STRIP_W-1 of rows by*strip_h .. +strip_h-1.
 template <typename T, typename R, int QS, bool FIELDS, int VAR = 0>
-__global__ void __launch_bounds__(STRIP_W, IsHalf<T>::value ? STRIP_MIN_BLOCKS_16 : STRIP_MIN_BLOCKS)
+__global__ void __launch_bounds__(STRIP_W, IsHalf<T>::value ? STRIP_MIN_BLOCKS_16
+                                           : (sizeof(R) == 8 ? STRIP_MIN_BLOCKS_64 : STRIP_MIN_BLOCKS))
     strip_kernel(const T* __restrict__ src, T* __restrict__ dst, R* __restrict__ prev, Geometry g,
                  Coeffs<R> C, unsigned* __restrict__ flag, uint32_t mask, void* __restrict__ out,
                  int out_f64) {
