@@ -511,7 +511,12 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
     rollout(sur, sims, 1)
     (out, _), t_nn = timed(lambda: rollout(sur, sims, hops))
     err_nn = field_errors(out.cpu().numpy(), truth5)
-    # judged hybrid
+    # judged hybrid (one untimed call first, as for the network, on separate
+    # lattices: the judge and the fallback step the solver's state)
+    sims_w, bw = fresh()
+    bw.close()
+    rollout(sur, sims_w, judge_every, judge_every=judge_every, tol=tol)
+    del sims_w
     (out_h, st), t_h = timed(lambda: rollout(sur, sims, hops, judge_every=judge_every, tol=tol))
     err_h = field_errors(out_h.cpu().numpy(), truth5)
     cells = B * H * W

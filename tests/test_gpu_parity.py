@@ -47,6 +47,14 @@ def _case(name):
                  visc_model=2, visc_beta=1.3)
         one = np.ones((H, 1))
         return p, ("fields", one, 0.5 * one, 0 * one), 500
+    if name == "narrow_x_walls":  # 3 columns between x walls: both wall columns and the
+        # single interior one in one warp, a body force along the channel
+        ny = 24
+        yy = np.arange(ny)[:, None] + np.zeros((1, 3))
+        phi = 0.5 + 0.5 * np.tanh((np.abs(yy - 11.5) - 6.0) / 2.0)
+        p = dict(wl.BASE, nx=3, ny=ny, wall_x=1, wall_y=0, mu1=0.1, mu2=0.03, rho2=0.3,
+                 Fy=2e-6, visc_model=2, visc_beta=0.8)
+        return p, ("fields", phi, 0.6 * phi, 0.2 * (1 - phi)), 300
     if name == "q9_logc_force":  # D2Q9 scalars, Eq. (48) viscosity, body force
         w = wl.droplet64(nx=40, ny=33, R=9.0, scalar_q=9, visc_model=1, mu1=0.2, mu2=0.05,
                          rho2=0.5, Fx=2e-6, gy=-1e-6, g_rho_ref=0.75)
@@ -55,7 +63,7 @@ def _case(name):
 
 
 CASES = ["droplet64", "planar_walls", "bubble_small", "ragged_periodic", "ragged_walls",
-         "strip_x", "strip_y_poiseuille", "q9_logc_force"]
+         "strip_x", "strip_y_poiseuille", "narrow_x_walls", "q9_logc_force"]
 
 _oracle_cache = {}
 
