@@ -320,13 +320,19 @@ class Surrogate:
                             self.net.s), "unpack")
 
 
-def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03, log=print):
+def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03, log=print,
+          pushforward=0.0):
     """Adam on the MSE of one hop over all consecutive snapshot pairs, with a
     cosine learning-rate decay.  The input state is corrupted by Gaussian noise
     of `noise` (normalised units) while the target stays the solver's: the
     network learns to pull a perturbed state back, which keeps its own
     autoregressive rollouts from drifting (input-noise training as in
-    Sanchez-Gonzalez et al. 2020)."""
+    Sanchez-Gonzalez et al. 2020).  With pushforward = q > 0, from the second
+    epoch on a fraction q of the batches starts one snapshot earlier: the
+    network's own (untrained-through) prediction of the next snapshot is the
+    input and the snapshot after it the target, so the network also learns
+    from the errors it makes itself (the pushforward trick of Brandstetter,
+    Worrall & Welling 2022)."""
     import torch
     net = sur.net
     n, S = data.shape[0], data.shape[1]
@@ -334,6 +340,7 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03,
     ws = Workspace(batch, H, W, net.device, train=True)
     L = nn_lib()
     pairs = np.array([(i, k) for i in range(n) for k in range(S - 1)])
+    triples = np.array([(i, k) for i in range(n) for k in range(S - 2)])
     g = np.random.default_rng(seed)
     steps = epochs * (len(pairs) // batch)
     losses = torch.zeros(max(1, steps), dtype=torch.float64, device=net.device)
@@ -344,14 +351,20 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03,
         order = g.permutation(len(pairs))
         lr_ep = lr * (0.5 * (1.0 + math.cos(math.pi * ep / max(1, epochs))))
         for b0 in range(0, len(order) - batch + 1, batch):
-            sel = pairs[order[b0:b0 + batch]]
+            push = pushforward > 0 and ep > 0 and len(triples) > 0 and g.random() < pushforward
+            sel = triples[g.integers(0, len(triples), batch)] if push else pairs[order[b0:b0 + batch]]
             ii = torch.from_numpy(sel[:, 0]).to(net.device)
             kk = torch.from_numpy(sel[:, 1]).to(net.device)
             xf = data[ii, kk].contiguous()
-            yf = data[ii, kk + 1].contiguous()
-            sur.pack(xf, ws, ws.x32, None if noise > 0 else ws.x16)
+            yf = data[ii, kk + (2 if push else 1)].contiguous()
+            sur.pack(xf, ws, ws.x32, ws.x16 if (push or noise <= 0) else None)
             sur.pack(yf, ws, ws.t32)
-            if noise > 0:
+            if push:
+                # the network's own hop as the input (no gradient through it)
+                net.forward(ws.x32, ws.x16, ws.y32, ws.acts, batch, H, W)
+                ws.x32.copy_(ws.y32)
+                _ck(L.lbm_nn_to_bf16(_p(ws.x32), ws.x32.numel(), _p(ws.x16), net.s), "to_bf16")
+            elif noise > 0:
                 _ck(L.lbm_nn_add_noise(_p(ws.x32), ws.P, USED, noise, (seed * 1000003 + step) & 0xffffffff,
                                        net.s), "noise")
                 _ck(L.lbm_nn_to_bf16(_p(ws.x32), ws.x32.numel(), _p(ws.x16), net.s), "to_bf16")
@@ -371,6 +384,17 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03,
                 % (ep, lh[-per:].mean(), lh[0], float(ident[:min(step, 8)].mean()), time.perf_counter() - t0))
     train.identity_loss = float(ident[:min(step, 8)].mean())
     return losses[:step].cpu().numpy()
+
+
+def field_rms_errors(got5, want5):
+    """Per channel: RMS of got - want over all nodes and cases, in the scales of
+    field_errors."""
+    got5, want5 = np.asarray(got5, np.float64), np.asarray(want5, np.float64)
+    speed = float(np.sqrt(want5[:, 1] ** 2 + want5[:, 2] ** 2).max())
+    scales = [float(np.abs(want5[:, 0]).max()), speed, speed, float(np.abs(want5[:, 3]).max()),
+              float(np.abs(want5[:, 4]).max())]
+    return {c: float(np.sqrt(np.mean((got5[:, k] - want5[:, k]) ** 2)) / max(scales[k], 1e-30))
+            for k, c in enumerate(CHANNELS)}
 
 
 def field_errors(got5, want5):
@@ -441,6 +465,7 @@ def rollout(sur: Surrogate, sims, hops, judge_every=0, tol=0.05, keq=None):
             _ck(L.lbm_nn_state_diff(_p(ws.y32), _p(lb32), B, H * W, _p(ws.diff_part), _p(ws.diff), net.s), "diff")
             rms = ws.diff.view(B, 5, 2)[:, :, 1].cpu().numpy()
             stats["judged"] += 1
+            stats.setdefault("judged_rms_max", []).append(float(np.nanmax(rms)) if np.isfinite(rms).any() else float("inf"))
             if np.all(np.isfinite(rms)) and float(rms.max()) <= tol:
                 ver32.copy_(ws.y32)
                 ver_pop = None
@@ -508,9 +533,16 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
     # the network alone (one untimed call first: allocations, first launches)
     sims, b = fresh()
     b.close()
+    for j, s in enumerate(sims):
+        s.fields(names=FIELDS6, dtype="f32", device=True, out=f6[j])
+    start = f6.cpu().numpy()
+    start5 = np.concatenate([start[:, :4], start[:, 4:5] + start[:, 5:6]], axis=1)
     rollout(sur, sims, 1)
     (out, _), t_nn = timed(lambda: rollout(sur, sims, hops))
-    err_nn = field_errors(out.cpu().numpy(), truth5)
+    out_np = out.cpu().numpy()
+    err_nn = field_errors(out_np, truth5)
+    rms_nn = field_rms_errors(out_np, truth5)
+    rms_none = field_rms_errors(start5, truth5)
     # judged hybrid (one untimed call first, as for the network, on separate
     # lattices: the judge and the fallback step the solver's state)
     sims_w, bw = fresh()
@@ -530,7 +562,8 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
         "solver_s": t_lb, "network_s": t_nn, "hybrid_s": t_h,
         "solver_mlups": mlups(t_lb), "network_mlups_equiv": mlups(t_nn), "hybrid_mlups_equiv": mlups(t_h),
         "speedup_network": t_lb / t_nn, "speedup_hybrid": t_lb / t_h,
-        "error_network": err_nn, "error_hybrid": err_h, "judge": dict(st, every=judge_every, tol=tol),
+        "error_network": err_nn, "error_network_rms": rms_nn, "error_no_change_rms": rms_none,
+        "error_hybrid": err_h, "judge": dict(st, every=judge_every, tol=tol),
         "conv_tflops": conv_flops(B, H, W) * hops / t_hop / 1e12,
     }
 
@@ -579,6 +612,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--side", type=int, default=256)
     ap.add_argument("--out", default="surrogate.npz")
+    ap.add_argument("--pushforward", type=float, default=0.5,
+                    help="train: fraction of batches (from the second epoch) fed the network's own hop")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     if args.command == "conv-bench":
@@ -597,7 +632,7 @@ def main():
                                                              time.perf_counter() - t0), flush=True)
     shift, scale = normalisation(data)
     sur = Surrogate(Net(dev, seed=0), shift, scale)
-    losses = train(sur, data, epochs=args.epochs, batch=args.batch, lr=args.lr)
+    losses = train(sur, data, epochs=args.epochs, batch=args.batch, lr=args.lr, pushforward=args.pushforward)
     sur.save(args.out)
     print(json.dumps({"trajectories": args.trajectories, "epochs": args.epochs, "first_loss": float(losses[0]),
                       "last_loss": float(losses[-100:].mean()), "no_change_loss": train.identity_loss,
