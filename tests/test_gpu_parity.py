@@ -219,3 +219,45 @@ def test_local_gradient_schemes_match_oracle(name, scheme, precision):
     got = sim.fields()
     assert_parity(got, want, TOL[precision], label="grad %d %s/%s" % (scheme, name, precision))
     assert_parity(got, want, TOL[precision], names=("rho", "mu"), label=name)
+
+
+def test_largest_lattice_8192x8192_windows_against_oracle():
+    """The largest configuration, 8192 x 8192 periodic droplets (16.4 GB of
+    state), in the benchmark's launch configuration.  After k steps a node
+    depends only on the initial state within a few nodes of it (the pull and
+    the stencils of the moments reach one node each per step), so the oracle
+    runs small windows of the same initial fields with a margin of 2k + 4
+    nodes and the window centres are compared node by node: at interface
+    points of each droplet and across the periodic corner."""
+    import torch
+    from paper_2402_15752_gb300 import Simulation
+    from _parity import MAIN_FIELDS
+    w = wl.droplets8192()
+    ny, nx = w.sdf.shape
+    k, half = 3, 16
+    margin = 2 * k + 4
+    phi = 0.5 + 0.5 * np.tanh(2.0 * w.sdf / w.params["W"])  # Eq. (2)
+    c1, c2 = w.c1_tilde * phi, w.c2_tilde * (1.0 - phi)
+    sim = Simulation(w.params, precision="fp32")
+    sim.init_fields(phi, c1, c2)
+    sim.step(k)
+    got_dev = sim.fields(names=MAIN_FIELDS + ("rho",), device=True)
+    centres = [(0, 0)]
+    for (cx, cy), r in zip(w.info["centres"], w.info["radii"]):
+        centres.append((int(cy) % ny, int(cx + r) % nx))
+    got_w, want_w = {n: [] for n in got_dev}, {n: [] for n in got_dev}
+    for cy, cx in centres:
+        iy = (cy + np.arange(-half - margin, half + margin)) % ny
+        ix = (cx + np.arange(-half - margin, half + margin)) % nx
+        n = 2 * (half + margin)
+        win = lambda a: a[np.ix_(iy, ix)]
+        o = run_oracle(dict(w.params, nx=n, ny=n), ("fields", win(phi), win(c1), win(c2)), k).fields()
+        ty = torch.from_numpy(iy[margin:margin + 2 * half]).to(got_dev["phi"].device)
+        tx = torch.from_numpy(ix[margin:margin + 2 * half]).to(got_dev["phi"].device)
+        for name, v in got_dev.items():
+            got_w[name].append(v.index_select(0, ty).index_select(1, tx).cpu().numpy())
+            want_w[name].append(o[name][margin:margin + 2 * half, margin:margin + 2 * half])
+    got = {n: np.concatenate(v, axis=1) for n, v in got_w.items()}
+    want = {n: np.concatenate(v, axis=1) for n, v in want_w.items()}
+    assert_parity(got, want, TOL["fp32"], label="droplets8192 windows/fp32")
+    sim.close()
