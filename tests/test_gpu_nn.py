@@ -263,9 +263,12 @@ def test_training_reduces_the_loss_and_rollout_judge_falls_back():
         sims.append(s)
     out, st = sg.rollout(sur, sims, hops=4, judge_every=2, tol=0.0)
     # every judged hop rejected: the solver reruns the two hops since the last verified state
-    assert st == {"judged": 2, "fallbacks": 2, "solver_steps": 2 * 16 + 2 * 32}
+    counts = ("judged", "fallbacks", "solver_steps")
+    assert {k: st[k] for k in counts} == {"judged": 2, "fallbacks": 2, "solver_steps": 2 * 16 + 2 * 32}
+    assert len(st["judged_rms_max"]) == 2 and all(v > 0 for v in st["judged_rms_max"])
     out2, st2 = sg.rollout(sur, sims, hops=4, judge_every=2, tol=float("inf"))
-    assert st2 == {"judged": 2, "fallbacks": 0, "solver_steps": 2 * 16} and bool(t.isfinite(out2).all())
+    assert {k: st2[k] for k in counts} == {"judged": 2, "fallbacks": 0, "solver_steps": 2 * 16}
+    assert bool(t.isfinite(out2).all())
 
 
 def test_what_the_network_gains_over_the_solver():
