@@ -53,12 +53,14 @@ extern "C" {
 #define LBM_FP64           0 /* FP64 storage and arithmetic                      */
 #define LBM_FP32           1 /* FP32 storage and arithmetic                      */
 /* 16-bit population storage, FP32 arithmetic: each population is read, converted
- * and collided in FP32 and rounded stochastically on the store (deterministic
- * hash bits, so runs and restarts are reproducible).  f is stored as the offset
- * f_i - w_i/2 from its value at phi = 1/2, g as it is (bfloat16) or as g_i * 2^10
- * (half), h as it is; the five previous-step macros stay FP32.  Not in the paper:
- * it halves the population bytes per node (112 -> 56 for scalar_q = 5) at a field
- * error of 1e-3..1e-2 (half); bfloat16 cannot carry density ratios near 1000. */
+ * and collided in FP32 and rounded stochastically on the store (the random bits
+ * are a hash seeded per node and step from the node's coordinates and new macros:
+ * deterministic, so runs and restarts are reproducible).  f is stored as the
+ * offset f_i - w_i/2 from its value at phi = 1/2, g as it is (bfloat16) or as
+ * g_i * 2^10 (half), h as it is; the five previous-step macros stay FP32.  Not in
+ * the paper: it halves the population bytes per node (112 -> 56 for scalar_q = 5)
+ * at a field error of 1e-3..1e-2 (half); bfloat16 cannot carry the density ratio
+ * 1000 bubble.  A step of a 16-bit run also reports a non-finite pressure. */
 #define LBM_FP32_BF16STORE 2 /* bfloat16 storage (8-bit significand, FP32 range)  */
 #define LBM_FP32_FP16STORE 3 /* IEEE half storage (11-bit significand, |x| < 65504;
                                 values below 6.1e-5 lose bits as subnormals)        */
