@@ -46,6 +46,9 @@ def parse_args():
                     choices=["bubble1024x2048", "droplets8192", "batched256"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"],
                     help="population storage (bf16/fp16: 16-bit storage, FP32 arithmetic)")
+    ap.add_argument("--cases", type=int, default=256, help="batched256: number of lattices (a smaller "
+                    "sample of the same generator, for profiling)")
+    ap.add_argument("--tiling", default=None, help="batched256: tile WxH instead of the autotuner's choice")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -368,14 +371,19 @@ def run_batched(args, rank, world, local):
         if world > 1:
             dist.barrier()
 
-    cases = wl.batched()
+    cases = wl.batched(n=args.cases)
     cells = sum(w.cells for w in cases)
     sims = [Simulation(w.params, precision="fp32", device=dev) for w in cases]
     for s, w in zip(sims, cases):
         s.init(w.sdf, w.c1_tilde, w.c2_tilde)
     stream = sims[0].stream
     b = Batch(sims)
-    tune = b.autotune(steps_per_trial=10)
+    if args.tiling:
+        tw, th = (int(v) for v in args.tiling.lower().split("x"))
+        b.set_tiling(tw, th)
+        tune = dict(b.tiling(), cached=False, trials=[], fixed=True)
+    else:
+        tune = b.autotune(steps_per_trial=10)
     b.step(max(3, args.warmup))
     b.sync()
 
