@@ -221,7 +221,17 @@ def test_local_gradient_schemes_match_oracle(name, scheme, precision):
     assert_parity(got, want, TOL[precision], names=("rho", "mu"), label=name)
 
 
-def test_largest_lattice_8192x8192_windows_against_oracle():
+# 16-bit storage: a few steps from the rounded initial state.  phi and c carry
+# the storage's rounding; u and p, still tiny three steps after a state at rest,
+# are measured against their own small scale and carry the rounding noise of g
+# (about twice the measured errors)
+LARGEST_TOL = {"fp32": dict.fromkeys(("phi", "ux", "uy", "p", "c1", "c2"), TOL["fp32"]),
+               "fp16": dict(phi=6e-4, c1=1.3e-3, c2=1.3e-3, ux=0.05, uy=0.05, p=0.02),
+               "bf16": dict(phi=5e-3, c1=1.2e-2, c2=1.2e-2, ux=0.4, uy=0.4, p=0.08)}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_largest_lattice_8192x8192_windows_against_oracle(precision):
     """The largest configuration, 8192 x 8192 periodic droplets (16.4 GB of
     state), in the benchmark's launch configuration.  After k steps a node
     depends only on the initial state within a few nodes of it (the pull and
@@ -238,7 +248,7 @@ def test_largest_lattice_8192x8192_windows_against_oracle():
     margin = 2 * k + 4
     phi = 0.5 + 0.5 * np.tanh(2.0 * w.sdf / w.params["W"])  # Eq. (2)
     c1, c2 = w.c1_tilde * phi, w.c2_tilde * (1.0 - phi)
-    sim = Simulation(w.params, precision="fp32")
+    sim = Simulation(w.params, precision=precision)
     sim.init_fields(phi, c1, c2)
     sim.step(k)
     got_dev = sim.fields(names=MAIN_FIELDS + ("rho",), device=True)
@@ -259,5 +269,9 @@ def test_largest_lattice_8192x8192_windows_against_oracle():
             want_w[name].append(o[name][margin:margin + 2 * half, margin:margin + 2 * half])
     got = {n: np.concatenate(v, axis=1) for n, v in got_w.items()}
     want = {n: np.concatenate(v, axis=1) for n, v in want_w.items()}
-    assert_parity(got, want, TOL["fp32"], label="droplets8192 windows/fp32")
+    from _parity import rel_max_errors
+    errs = rel_max_errors(got, want)
+    print("\ndroplets8192 windows/%s %s" % (precision, " ".join("%s=%.1e" % kv for kv in errs.items())))
+    bad = {k: v for k, v in errs.items() if not v <= LARGEST_TOL[precision][k]}
+    assert not bad, (precision, bad)
     sim.close()
