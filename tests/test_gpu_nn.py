@@ -53,13 +53,14 @@ def _sync():
     _torch().cuda.synchronize()
 
 
+@pytest.mark.parametrize("H", [16, 64])  # two or eight tile rows per image
 @pytest.mark.parametrize("ci,co,epi", [(16, 48, sg.RELU), (48, 48, sg.RELU), (48, 16, sg.RESIDUAL),
                                        (48, 48, sg.MASK), (16, 48, sg.MASK)])
-def test_conv3x3_matches_the_fp64_reference(ci, co, epi):
+def test_conv3x3_matches_the_fp64_reference(ci, co, epi, H):
     t = _torch()
     L = sg.nn_lib()
-    g = np.random.default_rng(ci * 100 + co + epi)
-    B, H, W = 2, 16, 32
+    g = np.random.default_rng(ci * 100 + co + epi + H)
+    B, W = 2, 32
     x, xr = _bf16(g.standard_normal((B, H, W, ci)))
     w, wr = _bf16(g.standard_normal((co, 9, ci)) / np.sqrt(9 * ci))
     b = g.standard_normal(co).astype(np.float32)
