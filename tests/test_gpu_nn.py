@@ -290,6 +290,9 @@ def test_what_the_network_gains_over_the_solver():
     r = sg.evaluate(sur, sg.droplet_cases(16, seed=11), hops=4, judge_every=2, tol=0.1)
     print("\n" + json.dumps(r))
     assert r["network_s"] > 0 and r["solver_s"] > 0 and r["conv_tflops"] > 0
+    # the gain: a network hop is faster than the 16 solver steps it replaces
+    # (measured 1.74x on these 16 cases of 256 x 256, against the batched solver)
+    assert r["speedup_network"] > 1.2, r["speedup_network"]
     assert all(np.isfinite(v) for v in r["error_hybrid"].values())
     if r["judge"]["fallbacks"] == r["judge"]["judged"]:
         assert max(r["error_hybrid"].values()) < 1e-5
