@@ -12,6 +12,10 @@ physics fix (CPU only).
   D1 = D2 = K = 1)
 * the pseudo-single-phase case of Sec. IV A 1 (heat kernel)
 * Poiseuille flow u_max = G H^2 / (8 mu) for the three viscosity relations
+* the layered channel of Sec. IV C 2, and its density-ratio deviation converging
+  at second order in dx/W
+* hydrostatic pressure slopes of a two-density column (density and body force)
+* a light bubble rises under buoyancy
 * mirror/transpose symmetry of a centred droplet (catches swapped x/y terms)
 """
 import json
@@ -268,7 +272,11 @@ def test_centred_droplet_keeps_mirror_and_transpose_symmetry():
 
 
 # ------------------------------------------------------ layered Poiseuille --
-def layered_poiseuille_profile(params, y):
+def _cumtrapz(f, s):
+    return np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(s))])
+
+
+def layered_poiseuille_profile(params, y, kappa=0.0):
     """Steady velocity of the layered channel once the scalar has equilibrated
     (Sec. IV C 2): total scalar 1/2 everywhere, split at the Henry equilibrium
     (K = 1: c1 = phi / 2, c2 = (1 - phi) / 2), viscosity from Eq. (48), phi the
@@ -276,39 +284,144 @@ def layered_poiseuille_profile(params, y):
     d/dy (mu du/dy) = -G, integrates to mu du/dy = -G (y - y0); with no slip at
     both half-way walls y = -1/2 and y = ny - 1/2,
         u(y) = -G int_{-1/2}^{y} (s - y0) / mu(s) ds,  y0 = int s/mu / int 1/mu.
+    Density does not enter: the continuum balance holds for any rho(y).
+
+    kappa != 0 adds the interface truncation term of the discrete scheme.  The
+    second moment of G_i (Eq. 31) is there to cancel the u grad(rho) part of the
+    lattice's momentum flux (Chapman-Enskog: the viscous flux is
+    -(tau - 1/2)[div Q_eq - sum_i c_i c_i G_i], and both carry
+    c_s^2 (u grad rho + grad rho u)); the cancellation is exact in the
+    continuum but, on the lattice, only up to the truncation of the Eq. (41)
+    stencil (phi' + phi'''/6 in 1D) against the lattice's own difference of
+    rho u.  What is left is a shear stress nu u (rho1 - rho2) kappa phi''',
+    i.e. du/dy gains u (rho1 - rho2) kappa phi''' / rho: a velocity step across
+    the interface of relative size ~ kappa (dx/W)^2 ln(rho1/rho2), independent of
+    the channel height.  It is added as a first-order perturbation, u from the
+    profile above, y0 re-fitted to keep both walls at rest.
     Evaluated by the trapezoid rule on a fine grid (independent of the solver)."""
     ny, W, G = params["ny"], params["W"], params["Fx"]
+    r1, r2 = params["rho1"], params["rho2"]
     s = np.linspace(-0.5, ny - 0.5, 200001)
-    phi = 0.5 + 0.5 * np.tanh(2.0 * ((ny - 1) / 2.0 - s) / W)
+    t = np.tanh(2.0 * ((ny - 1) / 2.0 - s) / W)
+    phi = 0.5 + 0.5 * t
     c1, c2 = 0.5 * phi, 0.5 * (1.0 - phi)
     mu = np.exp(c1 * np.log(params["mu1"]) + c2 * np.log(params["mu2"]))
-    def cumtrapz(f):
-        return np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(s))])
-    y0 = cumtrapz(s / mu)[-1] / cumtrapz(1.0 / mu)[-1]
-    u = -G * cumtrapz((s - y0) / mu)
+    a, b = _cumtrapz(s / mu, s)[-1], _cumtrapz(1.0 / mu, s)[-1]
+    u = -G * _cumtrapz((s - a / b) / mu, s)
+    if kappa:
+        # phi = 1/2 + 1/2 tanh(k (y_i - s)), k = 2/W:
+        # phi''' = k^3 sech^2 (sech^2 - 2 tanh^2) (three factors -k from the chain rule)
+        k, sech2 = 2.0 / W, 1.0 - t * t
+        d3 = k ** 3 * sech2 * (sech2 - 2.0 * t * t)
+        rho = r2 + (r1 - r2) * phi
+        step = _cumtrapz(u * (r1 - r2) * kappa * d3 / rho, s)
+        u = -G * _cumtrapz((s - (a - step[-1] / G) / b) / mu, s) + step
     return np.interp(y, s, u)
 
 
-@pytest.mark.parametrize("rho1,bound", [(1.0, 0.02), (10.0, 0.10)])
-def test_layered_poiseuille_with_concentration_dependent_viscosity(rho1, bound):
-    """A shorter channel (ny = 40) so that the FP64 oracle reaches the steady
-    state in seconds; the GPU test runs the paper's 15 x 150.  With equal
-    densities the profile matches to 1.7 % (the diffuse interface); with the
-    paper's density ratio 10 the method as stated deviates by 7.7 %, and the
-    deviation does not shrink with the channel height (8.7 % at ny = 20, 7.2 % at
-    ny = 80, measured), so it is the model's, not the resolution's."""
-    w = wl.layered_poiseuille(nx=4, ny=40, D=0.5, rho1=rho1)
+def _layered_error(rho1, W, kappa=0.0, ny=40, steps=24000):
+    w = wl.layered_poiseuille(nx=4, ny=ny, D=0.5, rho1=rho1, W=W)
     s = oracle.OracleSim(w.params)
     s.init(w.sdf, 1.0, 0.0)
-    s.step(24000)
+    s.step(steps)
     f = s.fields()
     c = f["c1"] + f["c2"]
     assert np.abs(c - 0.5).max() < 2e-3  # the scalar has equilibrated
     ux = f["ux"].mean(axis=1)
-    want = layered_poiseuille_profile(w.params, np.arange(40.0))
-    err = np.abs(ux - want).max() / np.abs(want).max()
-    assert err < bound, err
-    assert np.abs(f["uy"]).max() < 1e-2 * np.abs(want).max()  # spurious currents only
+    plain = layered_poiseuille_profile(w.params, np.arange(float(ny)))
+    scale = np.abs(plain).max()
+    assert np.abs(f["uy"]).max() < 1e-2 * scale  # spurious currents only
+    err = np.abs(ux - plain).max() / scale
+    if not kappa:
+        return err
+    corr = layered_poiseuille_profile(w.params, np.arange(float(ny)), kappa)
+    return err, np.abs(ux - corr).max() / scale
+
+
+def test_layered_poiseuille_equal_densities():
+    """Sec. IV C 2 with rho1 = rho2 (ny = 40 so that the FP64 oracle reaches
+    the steady state in seconds; the GPU test runs the paper's 15 x 150): the
+    profile matches to 1.7 % of u_max, a uniform offset in phase 1 where
+    tau_g = 3.5: the wall slip of BGK half-way bounce-back, which is second
+    order in 1/H (0.43 % at ny = 80, measured)."""
+    assert _layered_error(1.0, 4.0) < 0.02
+
+
+def test_layered_poiseuille_density_ratio_10_converges_with_interface_width():
+    """Sec. IV C 2 at the paper's rho1/rho2 = 10.  The continuum balance does
+    not depend on rho; the discrete scheme leaves a velocity step at the
+    interface of relative size ~ (dx/W)^2 ln(rho1/rho2) (see
+    layered_poiseuille_profile), which does not shrink with the channel
+    height at fixed W in lattice units (7.7 % at ny = 40, 7.2 % at ny = 80) but
+    does with W, at second order.  Removing the second moment of G_i instead
+    gives 129 %; a swapped density is caught by the hydrostatic pins below.
+    The stencil's share of the step (kappa = 1/6, derived) removes most of the
+    deviation, with the right sign; kappa = 1/4 leaves 1.5 % at W = 4 and
+    0.16 % at W = 8 (ny = 80), so the lattice's own difference of rho u
+    supplies the rest, at the same order."""
+    e4, r4 = _layered_error(10.0, 4.0, kappa=1.0 / 6.0)
+    e8 = _layered_error(10.0, 8.0)
+    print("\nlayered rho ratio 10: W=4 %.4f (stencil term removed: %.4f), W=8 %.4f" % (e4, r4, e8))
+    assert 3.0 < e4 / e8 < 5.0, (e4, e8)  # second order in dx/W
+    assert e8 < 0.025
+    assert r4 < 0.5 * e4  # the derived stencil term explains most of it
+
+
+# ------------------------------------------- density and body force pins --
+@pytest.mark.parametrize("g_rho_ref", [0.0, 1.0])
+def test_hydrostatic_column_pins_density_and_body_force(g_rho_ref):
+    """A two-layer column at rest between walls, dense phase 1 (rho1 = 1) below
+    the light phase 2 (rho2 = 0.1), gravity g = -1e-5 along y, body force
+    G = (rho - rho_ref) g (Eq. 3b; rho_ref = 0 is the paper's rho g, rho_ref =
+    rho1 the buoyancy form of the rising bubble).  At rest the momentum balance
+    is hydrostatic, dp/dy = (rho - rho_ref) g, so the pressure slope in each
+    bulk phase fixes that phase's density (Eq. 6) and the sign and reference of
+    the force: a swapped rho1/rho2, a force of the wrong sign or the wrong
+    reference density each change a slope by 10 % or more.  Measured within
+    6e-4 of |rho1 g| after 8000 steps (nu = 0.5 damps the initial pressure
+    waves)."""
+    ny, g, r1, r2 = 48, -1e-5, 1.0, 0.1
+    p = dict(wl.BASE, nx=4, ny=ny, wall_y=1, sigma=0.01, rho1=r1, rho2=r2, mu1=0.5, mu2=0.05,
+             gy=g, g_rho_ref=g_rho_ref)
+    s = oracle.OracleSim(p)
+    s.init(wl.sdf_planar_y(4, ny, (ny - 1) / 2.0), 1.0, 0.0)
+    s.step(8000)
+    f = s.fields()
+    pr, y = f["p"].mean(axis=1), np.arange(float(ny))
+    dense, light = slice(4, ny // 2 - 8), slice(ny // 2 + 8, ny - 4)
+    slope1 = np.polyfit(y[dense], pr[dense], 1)[0]
+    slope2 = np.polyfit(y[light], pr[light], 1)[0]
+    tol = 2e-3 * abs(r1 * g)
+    assert abs(slope1 - (r1 - g_rho_ref) * g) < tol, slope1
+    assert abs(slope2 - (r2 - g_rho_ref) * g) < tol, slope2
+    assert np.abs(f["uy"]).max() < 1e-5 and np.abs(f["ux"]).max() < 1e-12
+
+
+def test_light_bubble_rises_under_buoyancy():
+    """A light bubble (phase 2, rho2 = 0.1 in rho1 = 1) in a closed box under
+    gravity -1e-5 along y with the buoyancy force of the rising-bubble case
+    (G = (rho - rho1) g, Sec. IV C 1) rises: its centroid moves up and its mean
+    vertical velocity is positive at every check (measured: +1.7 nodes in
+    3000 steps).  A sign error in the force or a swapped density makes it
+    sink."""
+    nx, ny = 48, 96
+    p = dict(wl.BASE, nx=nx, ny=ny, wall_x=1, wall_y=1, sigma=0.01, rho1=1.0, rho2=0.1,
+             mu1=0.1, mu2=0.01, gy=-1e-5, g_rho_ref=1.0)
+    s = oracle.OracleSim(p)
+    s.init(wl.sdf_bubble(nx, ny, nx / 2, ny / 4, 8.0), 0.0, 1.0)
+    y = np.arange(float(ny))[:, None]
+    def centroid():
+        f = s.fields()
+        b = 1.0 - f["phi"]
+        return float((b * y).sum() / b.sum()), float((b * f["uy"]).sum() / b.sum())
+    y0, _ = centroid()
+    ys = []
+    for _ in range(3):
+        s.step(1000)
+        yc, vy = centroid()
+        assert vy > 1e-4, vy
+        ys.append(yc)
+    assert y0 < ys[0] < ys[1] < ys[2] and ys[2] - y0 > 1.0, (y0, ys)
 
 
 # ------------------------------------------- one- vs two-scalar leakage --
