@@ -215,9 +215,10 @@ int64_t lbm_time(const lbm_handle* h);
  * All calls on a device share the array, so calls whose work overlaps on the GPU
  * (different streams, or different host threads) race: serialise them.  Every slot a
  * call reads is written by the same call first.
- * params: the parameters the state was created with (layout: nx, ny, scalar_q,
- * precision, boundaries).  d_state: device pointer, state_bytes >= its population
- * part.  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
+ * params: the parameters the state was created with; only the layout fields are read
+ * (nx, ny, bc_x, bc_y, scalar_q, precision, scalar_model), the physical ones are
+ * ignored, and an invalid layout field returns LBM_ERR_ARG.  d_state: device pointer,
+ * 16-byte aligned (LBM_ERR_ARG otherwise), state_bytes >= its population part.  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
  * host (the call synchronises the stream) or device (out_on_device != 0, asynchronous).
  * err: optional buffer of err_len bytes for an error message (may be NULL). */
 int lbm_conserved_noalloc(const lbm_params* params, const void* d_state, size_t state_bytes,

@@ -7,6 +7,7 @@
 #include "lbm_kernels.cuh"
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -16,6 +17,7 @@ constexpr int NA_THREADS = 256;
 constexpr long long NA_CHUNK = 8192;   // nodes per partial
 constexpr int NA_MAX_CHUNKS = 8192;    // => at most 8192 * 8192 = 67,108,864 nodes
 constexpr int NA_MAX_DEVICES = 64;
+constexpr uintptr_t NA_STATE_ALIGN = 16;
 
 // Scratch shared by every call on a device: partials then the two totals.
 // 2 * 8192 + 2 doubles = 131,088 bytes, held by each GPU that loads the library
@@ -125,9 +127,22 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     if (err && err_len) err[0] = '\0';
     if (!params || !d_state || !out)
         return na_fail(err, err_len, LBM_ERR_ARG, "params, state and out must be non-NULL");
-    // validate through the allocation-free sizing call (host only)
-    const size_t ws = lbm_workspace_bytes(params);
-    if (ws == 0) return na_fail(err, err_len, LBM_ERR_ARG, lbm_last_error(nullptr));
+    // Only the layout fields are read; the physical parameters do not enter a sum.
+    const lbm_params* p = params;
+    if (p->nx < 1 || p->ny < 1 || p->nx > (1 << 28) || p->ny > (1 << 28))
+        return na_fail(err, err_len, LBM_ERR_ARG, "nx and ny must be in [1, 2^28]");
+    if ((p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_WALL) || (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALL))
+        return na_fail(err, err_len, LBM_ERR_ARG, "bc_x/bc_y must be LBM_BC_PERIODIC or LBM_BC_WALL");
+    if (p->scalar_q != 5 && p->scalar_q != 9) return na_fail(err, err_len, LBM_ERR_ARG, "scalar_q must be 5 or 9");
+    if (p->precision < LBM_FP64 || p->precision > LBM_FP32_FP16STORE)
+        return na_fail(err, err_len, LBM_ERR_ARG, "unknown precision");
+    if (p->scalar_model != LBM_SCALAR_TWO && p->scalar_model != LBM_SCALAR_ONE)
+        return na_fail(err, err_len, LBM_ERR_ARG, "unknown scalar_model");
+    if (p->scalar_model == LBM_SCALAR_ONE && p->precision != LBM_FP64 && p->precision != LBM_FP32)
+        return na_fail(err, err_len, LBM_ERR_ARG, "the one-scalar model runs in LBM_FP64 or LBM_FP32");
+    // the kernels load 4- and 8-byte words: a misaligned state would fault the context
+    if (reinterpret_cast<uintptr_t>(d_state) % NA_STATE_ALIGN != 0)
+        return na_fail(err, err_len, LBM_ERR_ARG, "state must be 16-byte aligned");
     const long long nodes = (long long)params->nx * params->ny;
     const long long nchunks = (nodes + NA_CHUNK - 1) / NA_CHUNK;
     if (nchunks > NA_MAX_CHUNKS) {
