@@ -5,19 +5,23 @@
  * 16 time steps later, trained on trajectories of the solver itself, which
  * stays the fallback and the judge of the network's error.
  *
- * Tensors (device memory, caller-owned, row-major):
+ * Tensors (device memory, caller-owned, row-major, 16-byte aligned):
  *   activation  NHWC bfloat16 [batch][h][w][C], C = 16 or 48 channels
  *   state       NHWC float    [batch][h][w][16] (channels 0..4 used, rest zero)
  *   weights     bfloat16 [cout][9][cin], tap t = 3 (dy + 1) + (dx + 1)
  *   bias        float [cout]
- * A 3x3 convolution is periodic in both directions (the lattices are periodic):
- *   y[n, i, j, o] = b[o] + sum_{t, c} w[o, t, c] x[n, (i + dy_t) mod h, (j + dx_t) mod w, c].
+ * A 3x3 convolution with dilation d is periodic in both directions (the
+ * lattices are periodic):
+ *   y[n, i, j, o] = b[o] + sum_{t, c} w[o, t, c] x[n, (i + d dy_t) mod h, (j + d dx_t) mod w, c].
  * Products are formed from bfloat16 operands and accumulated in FP32 on the
- * tensor cores (mma.sync m16n8k16).
- * Shapes: h a multiple of 8, w a multiple of 16, (cin, cout) in {(16, 48),
- * (48, 48), (48, 16)}.  Every call is asynchronous on `stream` (a cudaStream_t,
- * NULL = legacy default) and returns LBM_OK (0), LBM_ERR_ARG (-1) for a bad
- * shape or pointer, or LBM_ERR_CUDA (-4) if a launch failed.
+ * 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
+ * Shapes: w a multiple of 128, 1 <= d <= 8, h a multiple of d, (cin, cout) in
+ * {(16, 48), (48, 48), (48, 16)}.  status: a device int32 that the kernels OR
+ * bit 0 into if one of their bounded waits on the tensor cores gives up (the
+ * result is then incomplete); the caller clears and reads it.  Every call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = legacy default) and returns
+ * LBM_OK (0), LBM_ERR_ARG (-1) for a bad shape, pointer or alignment, or
+ * LBM_ERR_CUDA (-4) if a launch failed.
  */
 #ifndef PFLBM_LBM_NN_H
 #define PFLBM_LBM_NN_H
@@ -33,26 +37,29 @@ extern "C" {
 #define LBM_NN_RESIDUAL 1 /* y = residual + conv + b, float state (cout = 16)          */
 #define LBM_NN_MASK     2 /* y = conv * (mask > 0), bfloat16 (backward through a ReLU) */
 
-/* 3x3 periodic convolution with a fused epilogue (see LBM_NN_*).  residual: float
- * state for LBM_NN_RESIDUAL; mask: bfloat16 activation with cout channels for
- * LBM_NN_MASK (the forward output of the ReLU the gradient flows back through);
- * bias may be NULL for LBM_NN_MASK. */
+/* 3x3 periodic convolution with dilation `dilation` and a fused epilogue (see
+ * LBM_NN_*).  residual: float state for LBM_NN_RESIDUAL; mask: bfloat16 activation
+ * with cout channels for LBM_NN_MASK (the forward output of the ReLU the gradient
+ * flows back through); bias may be NULL for LBM_NN_MASK. */
 int lbm_nn_conv3x3(const void* x, int32_t cin, const void* weights, const float* bias,
                    int32_t cout, int32_t epilogue, const float* residual, const void* mask,
-                   void* y, int32_t batch, int32_t h, int32_t w, void* stream);
+                   void* y, int32_t batch, int32_t h, int32_t w, int32_t dilation,
+                   int32_t* status, void* stream);
 
 /* Weights of the adjoint convolution: wt[c][t][o] = w[o][8 - t][c], so that the
  * gradient with respect to a convolution's input is lbm_nn_conv3x3 of the
- * output gradient with wt (cin and cout swapped). */
+ * output gradient with wt (cin and cout swapped, the same dilation). */
 int lbm_nn_flip_weights(const void* w, int32_t cin, int32_t cout, void* wt, void* stream);
 
-/* Weight gradient dw[o][t][c] = sum_{n,i,j} dy[n,i,j,o] x[n,(i+dy_t),(j+dx_t),c]
- * (float, overwritten), reduced in a fixed order through `partials`
- * (lbm_nn_wgrad_partial_bytes bytes of device scratch). */
-size_t lbm_nn_wgrad_partial_bytes(int32_t cin, int32_t cout, int32_t batch, int32_t h, int32_t w);
+/* Weight gradient dw[o][t][c] = sum_{n,i,j} dy[n,i,j,o] x[n,(i+d dy_t),(j+d dx_t),c]
+ * (float, overwritten), one partial per CTA reduced in a fixed order through
+ * `partials` (lbm_nn_wgrad_partial_bytes bytes of device scratch, which depends
+ * on the current device's SM count): deterministic. */
+size_t lbm_nn_wgrad_partial_bytes(int32_t cin, int32_t cout, int32_t batch, int32_t h, int32_t w,
+                                  int32_t dilation);
 int lbm_nn_conv3x3_wgrad(const void* x, int32_t cin, const void* dy, int32_t cout, float* dw,
                          void* partials, size_t partial_bytes, int32_t batch, int32_t h,
-                         int32_t w, void* stream);
+                         int32_t w, int32_t dilation, int32_t* status, void* stream);
 
 /* Bias gradient db[o] = sum over pixels of dy[., o] (float, overwritten), fixed
  * order through `partials` (>= 1024 * cout floats). */

@@ -32,6 +32,7 @@ from .lbm import LBMError, Simulation, load_library
 from . import workloads as wl
 
 LAYERS = ((16, 48), (48, 48), (48, 48), (48, 48), (48, 48), (48, 16))
+DILATIONS = (1, 1, 1, 1, 1, 1)
 HOP = 16
 USED = 5
 CHANNELS = ("phi", "ux", "uy", "p", "C")
@@ -45,9 +46,9 @@ def nn_lib():
         return L
     vp, i32, i64, sz, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_float
     sig = {
-        "lbm_nn_conv3x3": [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, i32, i32, vp],
+        "lbm_nn_conv3x3": [vp, i32, vp, vp, i32, i32, vp, vp, vp, i32, i32, i32, i32, vp, vp],
         "lbm_nn_flip_weights": [vp, i32, i32, vp, vp],
-        "lbm_nn_conv3x3_wgrad": [vp, i32, vp, i32, vp, vp, sz, i32, i32, i32, vp],
+        "lbm_nn_conv3x3_wgrad": [vp, i32, vp, i32, vp, vp, sz, i32, i32, i32, i32, vp, vp],
         "lbm_nn_bias_grad": [vp, i32, i64, vp, vp, vp],
         "lbm_nn_mse": [vp, vp, i32, i64, vp, vp, vp, vp],
         "lbm_nn_adam": [vp, vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp],
@@ -63,7 +64,7 @@ def nn_lib():
         fn.restype = ctypes.c_int
         fn.argtypes = args
     L.lbm_nn_wgrad_partial_bytes.restype = sz
-    L.lbm_nn_wgrad_partial_bytes.argtypes = [i32, i32, i32, i32, i32]
+    L.lbm_nn_wgrad_partial_bytes.argtypes = [i32, i32, i32, i32, i32, i32]
     L._nn_ready = True
     return L
 
@@ -93,11 +94,15 @@ def to_device_bf16(a: np.ndarray, device):
 class Net:
     """Parameters, optimiser state and scratch of the six-layer network."""
 
-    def __init__(self, device, seed: int = 0, stream=None):
+    def __init__(self, device, seed: int = 0, stream=None, dilations=DILATIONS):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.dil = tuple(int(d) for d in dilations)
+        assert len(self.dil) == len(LAYERS)
+        # bit 0 set by a convolution whose bounded wait on the tensor cores gave up
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         g = np.random.default_rng(seed)
         self.w32, self.b32, self.wb, self.wt = [], [], [], []
         self.mw, self.vw, self.mb, self.vb, self.gw, self.gb = [], [], [], [], [], []
@@ -141,8 +146,13 @@ class Net:
             _ck(L.lbm_nn_flip_weights(_p(self.wb[l]), ci, co, _p(self.wt[l]), self.s), "flip")
 
     # -- save / load (FP32 master weights) --
+    def check(self):
+        """Raise if a convolution reported that a bounded wait gave up."""
+        if int(self.status.item()) != 0:
+            raise LBMError(-6, "surrogate convolution: a wait on the tensor cores timed out")
+
     def state_dict(self) -> dict:
-        out = {}
+        out = {"dilations": np.asarray(self.dil, dtype=np.int32)}
         for l in range(6):
             out["w%d" % l] = self.w32[l].cpu().numpy()
             out["b%d" % l] = self.b32[l].cpu().numpy()
@@ -167,10 +177,10 @@ class Net:
             ci, co = LAYERS[l]
             nxt = acts[l] if len(acts) == 5 else acts[l % 2]
             _ck(L.lbm_nn_conv3x3(_p(cur), ci, _p(self.wb[l]), _p(self.b32[l]), co, RELU, None, None,
-                                 _p(nxt), B, H, W, self.s), "conv%d" % l)
+                                 _p(nxt), B, H, W, self.dil[l], _p(self.status), self.s), "conv%d" % l)
             cur = nxt
         _ck(L.lbm_nn_conv3x3(_p(cur), 48, _p(self.wb[5]), _p(self.b32[5]), 16, RESIDUAL, _p(x32), None,
-                             _p(out32), B, H, W, self.s), "conv5")
+                             _p(out32), B, H, W, self.dil[5], _p(self.status), self.s), "conv5")
 
     def backward(self, x16, acts, dz16, dbuf, scratch, B, H, W):
         """Gradients of every weight and bias from dz16 = d loss / d out (bf16, 16 ch)."""
@@ -181,14 +191,14 @@ class Net:
         for l in range(5, -1, -1):
             ci, co = LAYERS[l]
             a_l = x16 if l == 0 else acts[l - 1]
-            nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W)
-            _ck(L.lbm_nn_conv3x3_wgrad(_p(a_l), ci, _p(dz), co, _p(self.gw[l]), _p(wpart), nb, B, H, W, self.s),
-                "wgrad%d" % l)
+            nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W, self.dil[l])
+            _ck(L.lbm_nn_conv3x3_wgrad(_p(a_l), ci, _p(dz), co, _p(self.gw[l]), _p(wpart), nb, B, H, W,
+                                       self.dil[l], _p(self.status), self.s), "wgrad%d" % l)
             _ck(L.lbm_nn_bias_grad(_p(dz), co, P, _p(self.gb[l]), _p(bpart), self.s), "bgrad%d" % l)
             if l > 0:
                 nxt = dbuf[l % 2]
                 _ck(L.lbm_nn_conv3x3(_p(dz), co, _p(self.wt[l]), None, ci, MASK, None, _p(a_l), _p(nxt),
-                                     B, H, W, self.s), "dgrad%d" % l)
+                                     B, H, W, self.dil[l], _p(self.status), self.s), "dgrad%d" % l)
                 dz = nxt
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -205,7 +215,7 @@ class Net:
 class Workspace:
     """Device buffers for batches of B samples of H x W."""
 
-    def __init__(self, B, H, W, device, train=True):
+    def __init__(self, B, H, W, device, train=True, dilations=DILATIONS):
         import torch
         t = torch
         self.B, self.H, self.W = B, H, W
@@ -219,7 +229,7 @@ class Workspace:
         self.acts = [t.empty((B, H, W, 48), dtype=t.bfloat16, device=device) for _ in range(nacts)]
         self.dbuf = [t.empty((B, H, W, 48), dtype=t.bfloat16, device=device) for _ in range(2)] if train else None
         L = nn_lib()
-        wbytes = max(L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W) for ci, co in LAYERS)
+        wbytes = max(L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W, d) for (ci, co), d in zip(LAYERS, dilations))
         self.scratch = (t.empty(wbytes // 4 + 1, dtype=t.float32, device=device),
                         t.empty(1024 * 48, dtype=t.float32, device=device))
         self.loss_part = t.empty(1024, dtype=t.float64, device=device)
@@ -301,7 +311,7 @@ class Surrogate:
     @classmethod
     def load(cls, path, device, stream=None):
         d = dict(np.load(path))
-        net = Net(device, stream=stream)
+        net = Net(device, stream=stream, dilations=tuple(d.get("dilations", DILATIONS)))
         net.load_state_dict(d)
         return cls(net, d["shift"], d["scale"])
 
@@ -337,7 +347,7 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03,
     net = sur.net
     n, S = data.shape[0], data.shape[1]
     H, W = data.shape[3], data.shape[4]
-    ws = Workspace(batch, H, W, net.device, train=True)
+    ws = Workspace(batch, H, W, net.device, train=True, dilations=net.dil)
     L = nn_lib()
     pairs = np.array([(i, k) for i in range(n) for k in range(S - 1)])
     triples = np.array([(i, k) for i in range(n) for k in range(S - 2)])
@@ -380,10 +390,13 @@ def train(sur: Surrogate, data, epochs=4, batch=16, lr=1e-3, seed=0, noise=0.03,
         if log:
             lh = losses[:step].cpu().numpy()
             per = max(1, len(order) // batch)
+            net.check()
             log("epoch %d: loss %.4e (first %.4e, no-change baseline %.4e)  %.1f s"
                 % (ep, lh[-per:].mean(), lh[0], float(ident[:min(step, 8)].mean()), time.perf_counter() - t0))
     train.identity_loss = float(ident[:min(step, 8)].mean())
-    return losses[:step].cpu().numpy()
+    out = losses[:step].cpu().numpy()
+    net.check()
+    return out
 
 
 def field_rms_errors(got5, want5):
@@ -423,7 +436,7 @@ def rollout(sur: Surrogate, sims, hops, judge_every=0, tol=0.05, keq=None):
     net = sur.net
     B = len(sims)
     H, W = sims[0].ny, sims[0].nx
-    ws = Workspace(B, H, W, net.device, train=False)
+    ws = Workspace(B, H, W, net.device, train=False, dilations=net.dil)
     L = nn_lib()
     f6 = torch.empty((B, 6, H, W), dtype=torch.float32, device=net.device)
     for j, s in enumerate(sims):
@@ -554,9 +567,10 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
     cells = B * H * W
     mlups = lambda t: cells * HOP * hops / t / 1e6
     # the hop's convolutions alone: achieved tensor throughput
-    ws = Workspace(B, H, W, dev, train=False)
+    ws = Workspace(B, H, W, dev, train=False, dilations=sur.net.dil)
     sur.hop(ws)
     _, t_hop = timed(lambda: [sur.hop(ws) for _ in range(hops)])
+    sur.net.check()
     return {
         "cases": B, "shape": [H, W], "hops": hops, "steps_per_hop": HOP,
         "solver_s": t_lb, "network_s": t_nn, "hybrid_s": t_h,
@@ -568,9 +582,10 @@ def evaluate(sur: Surrogate, cases, hops=8, judge_every=4, tol=0.1, warm=64):
     }
 
 
-def conv_bench(B=16, H=256, W=256, launches=20):
-    """Time the 48 -> 48 ReLU convolution alone (CUDA events); returns
-    (ms per launch, TFLOP/s)."""
+def conv_bench(B=16, H=256, W=256, launches=20, dilation=1, kind="fwd"):
+    """Time one 48 -> 48 convolution alone (CUDA events): the forward ReLU
+    convolution (kind "fwd"), the masked adjoint ("dgrad") or the weight
+    gradient ("wgrad"); returns (ms per launch, TFLOP/s)."""
     import torch
     L = nn_lib()
     dev = torch.device("cuda", 0)
@@ -580,9 +595,19 @@ def conv_bench(B=16, H=256, W=256, launches=20):
     b = torch.zeros(48, dtype=torch.float32, device=dev)
     y = torch.empty_like(x)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    nb = L.lbm_nn_wgrad_partial_bytes(48, 48, B, H, W, dilation)
+    part = torch.empty(nb // 4 + 1, dtype=torch.float32, device=dev)
+    dw = torch.empty((48, 9, 48), dtype=torch.float32, device=dev)
 
     def run():
-        _ck(L.lbm_nn_conv3x3(_p(x), 48, _p(w), _p(b), 48, RELU, None, None, _p(y), B, H, W, s), "conv")
+        if kind == "fwd":
+            rc = L.lbm_nn_conv3x3(_p(x), 48, _p(w), _p(b), 48, RELU, None, None, _p(y), B, H, W, dilation, _p(st), s)
+        elif kind == "dgrad":
+            rc = L.lbm_nn_conv3x3(_p(x), 48, _p(w), None, 48, MASK, None, _p(x), _p(y), B, H, W, dilation, _p(st), s)
+        else:
+            rc = L.lbm_nn_conv3x3_wgrad(_p(x), 48, _p(x), 48, _p(dw), _p(part), nb, B, H, W, dilation, _p(st), s)
+        _ck(rc, "conv")
 
     for _ in range(3):
         run()
@@ -594,6 +619,8 @@ def conv_bench(B=16, H=256, W=256, launches=20):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / launches
+    if int(st.item()) != 0:
+        raise LBMError(-6, "conv-bench: a wait on the tensor cores timed out")
     return ms, 2.0 * B * H * W * 9 * 48 * 48 / ms / 1e9
 
 
@@ -612,13 +639,16 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--side", type=int, default=256)
     ap.add_argument("--out", default="surrogate.npz")
+    ap.add_argument("--dilation", type=int, default=1, help="conv-bench: dilation of the timed convolution")
     ap.add_argument("--pushforward", type=float, default=0.5,
                     help="train: fraction of batches (from the second epoch) fed the network's own hop")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     if args.command == "conv-bench":
-        ms, tf = conv_bench()
-        print("conv 48->48, batch 16 of 256 x 256: %.3f ms, %.1f TFLOP/s" % (ms, tf))
+        for kind in ("fwd", "dgrad", "wgrad"):
+            ms, tf = conv_bench(kind=kind, dilation=args.dilation)
+            print("conv 48->48 %s, dilation %d, batch 16 of 256 x 256: %.4f ms, %.1f TFLOP/s"
+                  % (kind, args.dilation, ms, tf))
         return
     if args.command == "evaluate":
         sur = Surrogate.load(args.model, dev)

@@ -53,19 +53,29 @@ def _sync():
     _torch().cuda.synchronize()
 
 
-@pytest.mark.parametrize("H", [16, 64])  # two or eight tile rows per image
+def _status():
+    t = _torch()
+    return t.zeros(1, dtype=t.int32, device="cuda")
+
+
+# (H, W, dilation): four rows per work unit or one (H / d not a multiple of 4),
+# one or two 128-pixel column blocks, halos that wrap across the image
+SHAPES = [(8, 128, 1), (24, 256, 2), (6, 128, 3), (32, 128, 8)]
+
+
+@pytest.mark.parametrize("H,W,dil", SHAPES)
 @pytest.mark.parametrize("ci,co,epi", [(16, 48, sg.RELU), (48, 48, sg.RELU), (48, 16, sg.RESIDUAL),
                                        (48, 48, sg.MASK), (16, 48, sg.MASK)])
-def test_conv3x3_matches_the_fp64_reference(ci, co, epi, H):
+def test_conv3x3_matches_the_fp64_reference(ci, co, epi, H, W, dil):
     t = _torch()
     L = sg.nn_lib()
-    g = np.random.default_rng(ci * 100 + co + epi + H)
-    B, W = 2, 32
+    g = np.random.default_rng(ci * 100 + co + epi + H + dil)
+    B = 2
     x, xr = _bf16(g.standard_normal((B, H, W, ci)))
     w, wr = _bf16(g.standard_normal((co, 9, ci)) / np.sqrt(9 * ci))
     b = g.standard_normal(co).astype(np.float32)
-    ref = cr.conv3x3(xr, wr, None if epi == sg.MASK else b)
-    bound = cr.conv3x3(np.abs(xr), np.abs(wr)) + np.abs(b)  # sum of |terms|
+    ref = cr.conv3x3(xr, wr, None if epi == sg.MASK else b, dil)
+    bound = cr.conv3x3(np.abs(xr), np.abs(wr), dil=dil) + np.abs(b)  # sum of |terms|
     res = mask = None
     if epi == sg.RESIDUAL:
         r = g.standard_normal((B, H, W, co)).astype(np.float32)
@@ -79,9 +89,12 @@ def test_conv3x3_matches_the_fp64_reference(ci, co, epi, H):
         else:
             mask, mr = _bf16(np.maximum(g.standard_normal((B, H, W, co)), 0.0))
             ref = ref * (mr > 0)
-    rc = L.lbm_nn_conv3x3(_p(x), ci, _p(w), _p(_f32(b)), co, epi, _p(res), _p(mask), _p(y), B, H, W, _stream())
+    st = _status()
+    rc = L.lbm_nn_conv3x3(_p(x), ci, _p(w), _p(_f32(b)), co, epi, _p(res), _p(mask), _p(y), B, H, W, dil,
+                          _p(st), _stream())
     assert rc == 0
     got = _host(y)
+    assert int(st.item()) == 0
     tol = 1e-5 * bound + (0.0 if epi == sg.RESIDUAL else U_BF16 * np.abs(ref)) + 1e-30
     assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
 
@@ -89,50 +102,111 @@ def test_conv3x3_matches_the_fp64_reference(ci, co, epi, H):
 def test_conv3x3_rejects_unsupported_shapes():
     t = _torch()
     L = sg.nn_lib()
-    x = t.zeros((1, 12, 32, 48), dtype=t.bfloat16, device="cuda")
+    x = t.zeros((1, 16, 256, 48), dtype=t.bfloat16, device="cuda")
     w = t.zeros((48, 9, 48), dtype=t.bfloat16, device="cuda")
     y = t.zeros_like(x)
-    assert L.lbm_nn_conv3x3(_p(x), 48, _p(w), None, 48, sg.RELU, None, None, _p(y), 1, 12, 32, None) == -1
-    assert L.lbm_nn_conv3x3(_p(x), 32, _p(w), None, 48, sg.RELU, None, None, _p(y), 1, 16, 32, None) == -1
+    st = _status()
+    ok = L.lbm_nn_conv3x3(_p(x), 48, _p(w), None, 48, sg.RELU, None, None, _p(y), 1, 16, 256, 1, _p(st), None)
+    assert ok == 0
+    _sync()
+    bad = [
+        dict(w_=96),        # width not a multiple of 128
+        dict(ci=32),        # unsupported channel count
+        dict(dil=0), dict(dil=9), dict(h=15, dil=2),  # dilation out of range, height not a multiple of it
+        dict(xoff=2),       # misaligned activation
+        dict(st=None),      # no status word
+    ]
+    for b in bad:
+        xp = ctypes.c_void_p(x.data_ptr() + b.get("xoff", 0))
+        rc = L.lbm_nn_conv3x3(xp, b.get("ci", 48), _p(w), None, 48, sg.RELU, None, None, _p(y), 1, b.get("h", 16),
+                              b.get("w_", 256), b.get("dil", 1), None if "st" in b else _p(st), None)
+        assert rc == -1, b
 
 
+@pytest.mark.parametrize("H,W,dil", [(8, 128, 1), (24, 256, 2), (6, 128, 3)])
 @pytest.mark.parametrize("ci,co", [(16, 48), (48, 48), (48, 16)])
-def test_weight_and_bias_gradients_match_the_reference(ci, co):
+def test_weight_and_bias_gradients_match_the_reference(ci, co, H, W, dil):
     t = _torch()
     L = sg.nn_lib()
-    g = np.random.default_rng(ci + 7 * co)
-    B, H, W = 2, 16, 48
+    g = np.random.default_rng(ci + 7 * co + H + dil)
+    B = 2
     x, xr = _bf16(g.standard_normal((B, H, W, ci)))
     dy, dyr = _bf16(g.standard_normal((B, H, W, co)))
-    nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W)
+    nb = L.lbm_nn_wgrad_partial_bytes(ci, co, B, H, W, dil)
+    assert nb > 0
     part = t.empty(nb // 4 + 1, dtype=t.float32, device="cuda")
     dw = t.empty((co, 9, ci), dtype=t.float32, device="cuda")
-    assert L.lbm_nn_conv3x3_wgrad(_p(x), ci, _p(dy), co, _p(dw), _p(part), nb, B, H, W, _stream()) == 0
-    ref = cr.conv3x3_wgrad(xr, dyr)
-    bound = cr.conv3x3_wgrad(np.abs(xr), np.abs(dyr))
-    assert np.all(np.abs(_host(dw) - ref) <= 1e-5 * bound + 1e-30)
+    st = _status()
+    assert L.lbm_nn_conv3x3_wgrad(_p(x), ci, _p(dy), co, _p(dw), _p(part), nb, B, H, W, dil, _p(st), _stream()) == 0
+    ref = cr.conv3x3_wgrad(xr, dyr, dil)
+    bound = cr.conv3x3_wgrad(np.abs(xr), np.abs(dyr), dil)
+    got = _host(dw)
+    assert int(st.item()) == 0
+    assert np.all(np.abs(got - ref) <= 1e-5 * bound + 1e-30), float(np.max(np.abs(got - ref) / (bound + 1e-30)))
     db = t.empty(co, dtype=t.float32, device="cuda")
     bpart = t.empty(1024 * co, dtype=t.float32, device="cuda")
     assert L.lbm_nn_bias_grad(_p(dy), co, B * H * W, _p(db), _p(bpart), _stream()) == 0
     np.testing.assert_allclose(_host(db), dyr.sum(axis=(0, 1, 2)), rtol=0, atol=1e-5 * np.abs(dyr).sum())
 
 
-def test_adjoint_convolution_through_flipped_weights():
-    """dgrad = conv of dy with the flipped weights (LBM_NN_MASK with an all-ones mask)."""
+@pytest.mark.parametrize("dil", [1, 2])
+def test_many_units_per_cta(dil):
+    """Enough work that every persistent CTA runs several units, so that the
+    pipelines wrap around their stages and tensor-memory buffers many times
+    (8 images of 128 x 256: 3-4 forward units and 6-7 weight-gradient units
+    per CTA on 152 SMs): forward, masked adjoint and weight gradient against
+    the FP64 reference."""
+    t = _torch()
+    L = sg.nn_lib()
+    g = np.random.default_rng(40 + dil)
+    B, H, W = 8, 128, 256
+    x, xr = _bf16(g.standard_normal((B, H, W, 48)))
+    w, wr = _bf16(g.standard_normal((48, 9, 48)) / np.sqrt(9 * 48))
+    b = g.standard_normal(48).astype(np.float32)
+    st = _status()
+    y = t.empty((B, H, W, 48), dtype=t.bfloat16, device="cuda")
+    assert L.lbm_nn_conv3x3(_p(x), 48, _p(w), _p(_f32(b)), 48, sg.RELU, None, None, _p(y), B, H, W, dil, _p(st),
+                            _stream()) == 0
+    ref = np.maximum(cr.conv3x3(xr, wr, b, dil), 0.0)
+    bound = cr.conv3x3(np.abs(xr), np.abs(wr), dil=dil) + np.abs(b)
+    assert np.all(np.abs(_host(y) - ref) <= 1e-5 * bound + U_BF16 * np.abs(ref))
+    mask, mr = _bf16(np.maximum(g.standard_normal((B, H, W, 48)), 0.0))
+    assert L.lbm_nn_conv3x3(_p(x), 48, _p(w), None, 48, sg.MASK, None, _p(mask), _p(y), B, H, W, dil, _p(st),
+                            _stream()) == 0
+    ref = cr.conv3x3(xr, wr, None, dil) * (mr > 0)
+    assert np.all(np.abs(_host(y) - ref) <= 1e-5 * bound + U_BF16 * np.abs(ref))
+    dy, dyr = _bf16(g.standard_normal((B, H, W, 48)))
+    nb = L.lbm_nn_wgrad_partial_bytes(48, 48, B, H, W, dil)
+    part = t.empty(nb // 4 + 1, dtype=t.float32, device="cuda")
+    dw = t.empty((48, 9, 48), dtype=t.float32, device="cuda")
+    assert L.lbm_nn_conv3x3_wgrad(_p(x), 48, _p(dy), 48, _p(dw), _p(part), nb, B, H, W, dil, _p(st), _stream()) == 0
+    ref = cr.conv3x3_wgrad(xr, dyr, dil)
+    wbound = cr.conv3x3_wgrad(np.abs(xr), np.abs(dyr), dil)
+    assert np.all(np.abs(_host(dw) - ref) <= 1e-5 * wbound)
+    assert int(st.item()) == 0
+
+
+@pytest.mark.parametrize("dil", [1, 2])
+def test_adjoint_convolution_through_flipped_weights(dil):
+    """dgrad = conv of dy with the flipped weights and the same dilation
+    (LBM_NN_MASK with an all-ones mask)."""
     t = _torch()
     L = sg.nn_lib()
     g = np.random.default_rng(3)
-    B, H, W = 1, 8, 16
+    B, H, W = 1, 8, 128
     w, wr = _bf16(g.standard_normal((48, 9, 48)) / 20)
     dy, dyr = _bf16(g.standard_normal((B, H, W, 48)))
     wt = t.empty((48, 9, 48), dtype=t.bfloat16, device="cuda")
     assert L.lbm_nn_flip_weights(_p(w), 48, 48, _p(wt), _stream()) == 0
     ones = t.ones((B, H, W, 48), dtype=t.bfloat16, device="cuda")
     dx = t.empty((B, H, W, 48), dtype=t.bfloat16, device="cuda")
-    assert L.lbm_nn_conv3x3(_p(dy), 48, _p(wt), None, 48, sg.MASK, None, _p(ones), _p(dx), B, H, W, _stream()) == 0
-    ref = cr.conv3x3_dgrad(dyr, wr)
-    bound = cr.conv3x3_dgrad(np.abs(dyr), np.abs(wr))
+    st = _status()
+    assert L.lbm_nn_conv3x3(_p(dy), 48, _p(wt), None, 48, sg.MASK, None, _p(ones), _p(dx), B, H, W, dil, _p(st),
+                            _stream()) == 0
+    ref = cr.conv3x3_dgrad(dyr, wr, dil)
+    bound = cr.conv3x3_dgrad(np.abs(dyr), np.abs(wr), dil)
     assert np.all(np.abs(_host(dx) - ref) <= 1e-5 * bound + U_BF16 * np.abs(ref))
+    assert int(st.item()) == 0
 
 
 def test_mse_and_adam_match_the_reference():
@@ -204,7 +278,7 @@ def test_network_gradients_match_the_fp64_backward():
     bound is 2.5e-2; against the plain FP64 reference (no bfloat16 storage
     between layers, measured 4.5e-4 .. 5.8e-2) it is 1e-1."""
     t = _torch()
-    B, H, W = 2, 16, 32
+    B, H, W = 1, 8, 128
     net = sg.Net("cuda", seed=5)
     ws = sg.Workspace(B, H, W, "cuda", train=True)
     g = np.random.default_rng(6)
@@ -240,12 +314,12 @@ def test_network_gradients_match_the_fp64_backward():
 
 
 def test_training_reduces_the_loss_and_rollout_judge_falls_back():
-    """A few hundred Adam steps on solver trajectories of 64 x 64 droplets cut
+    """A few hundred Adam steps on solver trajectories of 128 x 128 droplets cut
     the one-hop loss; the judged rollout falls back to the solver on every
     judged hop when the tolerance is zero, and never when it is infinite."""
     t = _torch()
     dev = t.device("cuda", 0)
-    cases = sg.droplet_cases(24, seed=1, side=64, radius=(5.0, 12.0))
+    cases = sg.droplet_cases(24, seed=1, side=128, radius=(10.0, 24.0))
     data = sg.generate(cases, snapshots=4, device=dev, warm=32)
     shift, scale = sg.normalisation(data)
     sur = sg.Surrogate(sg.Net(dev, seed=2), shift, scale)
@@ -255,7 +329,7 @@ def test_training_reduces_the_loss_and_rollout_judge_falls_back():
     assert np.all(np.isfinite(losses)) and last < 0.5 * first
     # judged rollout on 4 fresh lattices
     from paper_2402_15752_gb300 import Simulation
-    test_cases = sg.droplet_cases(4, seed=9, side=64, radius=(5.0, 12.0))
+    test_cases = sg.droplet_cases(4, seed=9, side=128, radius=(10.0, 24.0))
     sims = []
     for w in test_cases:
         s = Simulation(w.params, precision="fp32", device=dev)

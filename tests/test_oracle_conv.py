@@ -8,7 +8,7 @@ import pytest
 from oracle import conv_ref as cr
 
 
-def _brute_conv(x, w, b):
+def _brute_conv(x, w, b, dil=1):
     n, h, wd, ci = x.shape
     co = w.shape[0]
     y = np.zeros((n, h, wd, co))
@@ -20,41 +20,44 @@ def _brute_conv(x, w, b):
                     for t in range(9):
                         dy, dx = t // 3 - 1, t % 3 - 1
                         for c in range(ci):
-                            s += w[o, t, c] * x[a, (i + dy) % h, (j + dx) % wd, c]
+                            s += w[o, t, c] * x[a, (i + dil * dy) % h, (j + dil * dx) % wd, c]
                     y[a, i, j, o] = s
     return y
 
 
-def test_conv_matches_brute_force_loops():
+@pytest.mark.parametrize("dil", [1, 2, 3])
+def test_conv_matches_brute_force_loops(dil):
     g = np.random.default_rng(1)
-    x = g.standard_normal((2, 5, 6, 3))
+    x = g.standard_normal((2, 5, 7, 3))
     w = g.standard_normal((4, 9, 3))
     b = g.standard_normal(4)
-    np.testing.assert_allclose(cr.conv3x3(x, w, b), _brute_conv(x, w, b), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(cr.conv3x3(x, w, b, dil), _brute_conv(x, w, b, dil), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("dil", [1, 2])
 @pytest.mark.parametrize("t", range(9))
-def test_delta_kernel_shifts_the_input(t):
+def test_delta_kernel_shifts_the_input(t, dil):
     g = np.random.default_rng(2)
     x = g.standard_normal((1, 4, 5, 2))
     w = np.zeros((2, 9, 2))
     w[0, t, 0] = w[1, t, 1] = 1.0
     dy, dx = t // 3 - 1, t % 3 - 1
-    y = cr.conv3x3(x, w)
+    y = cr.conv3x3(x, w, dil=dil)
     for i in range(4):
         for j in range(5):
-            np.testing.assert_array_equal(y[0, i, j], x[0, (i + dy) % 4, (j + dx) % 5])
+            np.testing.assert_array_equal(y[0, i, j], x[0, (i + dil * dy) % 4, (j + dil * dx) % 5])
 
 
-def test_gradients_are_the_adjoints_of_the_convolution():
+@pytest.mark.parametrize("dil", [1, 2])
+def test_gradients_are_the_adjoints_of_the_convolution(dil):
     g = np.random.default_rng(3)
     x = g.standard_normal((2, 4, 6, 5))
     w = g.standard_normal((3, 9, 5))
     r = g.standard_normal((2, 4, 6, 3))
-    lhs = float((cr.conv3x3(x, w) * r).sum())
+    lhs = float((cr.conv3x3(x, w, dil=dil) * r).sum())
     # <conv(x; w), r> = <x, dgrad(r; w)> = <w, wgrad(x, r)>
-    assert lhs == pytest.approx(float((x * cr.conv3x3_dgrad(r, w)).sum()), rel=1e-12)
-    assert lhs == pytest.approx(float((w * cr.conv3x3_wgrad(x, r)).sum()), rel=1e-12)
+    assert lhs == pytest.approx(float((x * cr.conv3x3_dgrad(r, w, dil)).sum()), rel=1e-12)
+    assert lhs == pytest.approx(float((w * cr.conv3x3_wgrad(x, r, dil)).sum()), rel=1e-12)
 
 
 def _net(seed, h=4, w=8):
@@ -70,9 +73,10 @@ def _net(seed, h=4, w=8):
     return x, target, weights, biases
 
 
-def test_network_gradients_match_finite_differences():
-    x, target, weights, biases = _net(4)
-    loss, gw, gb = cr.net_loss_and_grads(x, target, weights, biases)
+@pytest.mark.parametrize("dil", [(1,) * 6, (1, 2, 3, 2, 1, 1)])
+def test_network_gradients_match_finite_differences(dil):
+    x, target, weights, biases = _net(4, h=6, w=8)
+    loss, gw, gb = cr.net_loss_and_grads(x, target, weights, biases, dil=dil)
     g = np.random.default_rng(5)
     eps = 1e-6
     for _ in range(24):
@@ -87,8 +91,8 @@ def test_network_gradients_match_finite_differences():
             wm = [v.copy() for v in weights]
             wp[l][o, t, c] += eps
             wm[l][o, t, c] -= eps
-            fd = (cr.net_loss_and_grads(x, target, wp, biases)[0]
-                  - cr.net_loss_and_grads(x, target, wm, biases)[0]) / (2 * eps)
+            fd = (cr.net_loss_and_grads(x, target, wp, biases, dil=dil)[0]
+                  - cr.net_loss_and_grads(x, target, wm, biases, dil=dil)[0]) / (2 * eps)
             assert gw[l][o, t, c] == pytest.approx(fd, rel=1e-5, abs=1e-9)
         else:
             o = int(g.integers(0, 5 if l == 5 else co))
@@ -96,8 +100,8 @@ def test_network_gradients_match_finite_differences():
             bm = [v.copy() for v in biases]
             bp[l][o] += eps
             bm[l][o] -= eps
-            fd = (cr.net_loss_and_grads(x, target, weights, bp)[0]
-                  - cr.net_loss_and_grads(x, target, weights, bm)[0]) / (2 * eps)
+            fd = (cr.net_loss_and_grads(x, target, weights, bp, dil=dil)[0]
+                  - cr.net_loss_and_grads(x, target, weights, bm, dil=dil)[0]) / (2 * eps)
             assert gb[l][o] == pytest.approx(fd, rel=1e-5, abs=1e-9)
     assert loss > 0
 
