@@ -168,16 +168,27 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     return sdesc(saddr, 16, 256) | ((uint64_t)LAYOUT_SW32 << 61);
 }
 
-// Roles (warp index): 0-3 epilogue (TMEM lane quarter = warp), 4 the TMA
-// issuer (lane 0), 5-7 halo loaders (warp 5 + h loads the halos of stages
-// q = h mod 3, so three stages' halo copies are in flight at once), 8 the MMA
-// issuer (lane 0) and owner of the tensor memory.
-constexpr int FW_EPI_WARPS = 4;
-constexpr int FW_TMA_WARP = 4, FW_HALO_WARP = 5, FW_HALO_WARPS = 3, FW_MMA_WARP = 8;
-constexpr int FW_THREADS = 32 * 9;
-// A row of a stage plane: 8 halo slots, the 128 pixels of the unit, 8 halo
-// slots (dilation <= 8); the unit's first pixel sits 256 bytes into the row.
-constexpr int FW_HALO = 8, FW_PITCH = TC_COLS + 2 * FW_HALO;
+// Roles of the forward kernel (warp index): 0-7 epilogue (warp w reads TMEM
+// lane quarter w % 4, output rows r = w / 4 mod 2), 8 the TMA issuer (lane 0),
+// 9-11 halo loaders (warp 9 + h loads the halos of stages q = h mod 3, so three
+// stages' halo copies are in flight at once), 12-13 the MMA issuers (lane 0;
+// warp 12 + p takes the units j = p mod 2 into accumulator buffer p: one thread
+// issues a tcgen05.mma only every ~90 cycles on GB300, two reach the tensor
+// cores' rate for these N <= 144 shapes (measured)); warp 12 owns the tensor memory.
+constexpr int FW_EPI_WARPS = 8;
+constexpr int FW_TMA_WARP = 8, FW_HALO_WARP = 9, FW_HALO_WARPS = 3, FW_MMA_WARP = 12, FW_MMA_WARPS = 2;
+constexpr int FW_THREADS = 32 * 14;
+// Roles of the weight-gradient kernel: 0-3 epilogue, 4 TMA, 5-7 halo, 8 MMA.
+constexpr int WG_TMA_WARP = 4, WG_HALO_WARP = 5, WG_HALO_WARPS = 3, WG_MMA_WARP = 8;
+constexpr int WG_THREADS = 32 * 9;
+// A row of a stage plane: HALO halo slots, the 128 pixels of the unit, HALO
+// halo slots (dilation <= HALO, 4 or 8); the unit's first pixel sits 32 HALO
+// bytes into the row (128-byte aligned, as the TMA wants).  The weight-gradient
+// kernel uses 8.
+constexpr int WG_HALO = 8, WG_PITCH = TC_COLS + 2 * WG_HALO;
+// Output staging of the forward kernel: per epilogue warp one row of its 32
+// pixels x 48 bfloat16 channels (3 KB), written to global memory by a TMA store.
+constexpr uint32_t FW_STG = 32 * 48 * 2;
 
 __device__ __forceinline__ void mbar_init_n(uint32_t mbar, uint32_t n) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(n) : "memory");
@@ -218,37 +229,60 @@ __device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[48]) {
     for (int j = 0; j < 48; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Whole warp: zero 16 consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
 __device__ __forceinline__ int image_row(const Unit& U, int k, int R, int d, int H) {
     int yy = U.rho + (U.rb * R + k - 1) * d;
     return yy + (yy < 0 ? H : (yy >= H ? -H : 0));
 }
 
-template <int CI, int CO, int EPI, int R, int S>
+// The three row taps (dy) share the A operand: for input row k of a unit, one
+// MMA multiplies the shifted row (dx) by the weights of all dy stacked along N
+// (rows ordered dy = +1, 0, -1), producing the contributions of that input row
+// to output rows k - 2, k - 1, k (those of the unit) in adjacent 48-column
+// blocks of tensor memory.  Output row i of a unit owns columns
+// [CO i, CO (i + 1)) of its buffer, so the three contributions to one output
+// row (from input rows i, i + 1, i + 2) accumulate on the same columns.  Half
+// the MMAs of one tap per MMA, each re-reading the 4 KB A tile for only 48 outputs.
+// Every MMA accumulates: the epilogue zeroes a buffer after reading it.
+template <int CI, int CO, int EPI, int R, int S, int HALO>
 __global__ void __launch_bounds__(FW_THREADS, 1)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, const uint8_t* __restrict__ x,
+    conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+                   const uint8_t* __restrict__ x,
                    const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias, void* __restrict__ y,
                    const float* __restrict__ res, const uint8_t* __restrict__ mask, int B, int H, int W, int d,
                    int* __restrict__ status) {
-    static_assert(CI % 16 == 0 && CO % 16 == 0 && CO <= 256, "bfloat16 UMMA shapes");
+    static_assert(CI % 16 == 0 && CO % 16 == 0 && 3 * CO <= 256, "bfloat16 UMMA shapes");
     constexpr int KB = CI / 16;                         // 16-channel planes of the input, K blocks per tap
     constexpr int NC = CI / 8;                          // 16-byte chunks per input pixel
     constexpr uint32_t WBYTES = 9u * CI * CO * 2u;
     constexpr uint32_t ACC = (uint32_t)R * CO;          // TMEM columns of one unit
     constexpr uint32_t TCOLS = pow2_cols(2 * ACC);
-    constexpr uint32_t IDESC = idesc_bf16(128, CO, 0, 0);
     // a pipeline stage holds one 16-channel plane of a unit: (R + 2) rows of
-    // FW_PITCH pixel slots, 32 bytes each (a multiple of 256 bytes)
-    constexpr uint32_t STAGE = (uint32_t)((R + 2) * FW_PITCH * 32);
+    // PITCH pixel slots, 32 bytes each (a multiple of 256 bytes)
+    constexpr int PITCH = TC_COLS + 2 * HALO;
+    constexpr uint32_t STAGE = (uint32_t)((R + 2) * PITCH * 32);
+    constexpr bool STAGED = CO == 48;                   // bfloat16 output through TMA stores
+    constexpr uint32_t STG = STAGED ? FW_EPI_WARPS * FW_STG : 0u;
     constexpr uint32_t TX = (uint32_t)((R + 2) * TC_COLS * 32);  // TMA bytes per stage
-    // halo warp h serves the stages s = h mod 3 only, so it waits on every phase
-    // of those stages' barriers in order (a parity wait cannot tell phases two apart)
-    static_assert(S % FW_HALO_WARPS == 0, "stages a multiple of the halo warps");
+    // halo warp h serves the stages s = h mod 3 only, and MMA warp p the stages
+    // of the units j = p mod 2, so each waits on every phase of its stages'
+    // barriers in order (a parity wait cannot tell phases two apart)
+    static_assert(S % FW_HALO_WARPS == 0 && S % (2 * KB) == 0, "stages owned by one halo and one MMA warp");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // [stages][weights][bias][barriers: full S, empty S, tfull 2, tempty 2][tmem slot]
+    // [stages][output staging][weights][bias][barriers: full S, empty S, tfull 2, tempty 2][tmem slot]
     const uint32_t base = smem_u32(smem);
-    const uint32_t sin0 = base, sw0 = base + S * STAGE;
-    float* s_bias = reinterpret_cast<float*>(smem + S * STAGE + WBYTES);
+    const uint32_t sin0 = base, sstg = base + S * STAGE, sw0 = sstg + STG;
+    float* s_bias = reinterpret_cast<float*>(smem + S * STAGE + STG + WBYTES);
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_bias + CO);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(s_bar + 2 * S + 4);
     auto full = [&](int s) { return smem_u32(&s_bar[s]); };
@@ -256,11 +290,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     auto tfull = [&](int b) { return smem_u32(&s_bar[2 * S + b]); };
     auto tempty = [&](int b) { return smem_u32(&s_bar[2 * S + 2 + b]); };
 
-    // weights [co][t][ci] -> blocks (t, 16-channel group) of CO rows x 32 bytes, swizzled
+    // weights [co][t][ci] -> blocks (dx, 16-channel group) of 3 CO rows x 32
+    // bytes, swizzled; row bi CO + o of a block holds tap dy = 1 - bi
     for (int i = tid; i < 9 * NC * CO; i += FW_THREADS) {
-        const int o = i % CO, pl = i / CO, t = pl / NC, j = pl % NC;
+        const int o = i % CO, rest = i / CO, j = rest % NC, tap = rest / NC;  // tap = 3 bi + dxi
+        const int bi = tap / 3, dxi = tap % 3, t = 3 * (2 - bi) + dxi;
         const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)o * 9 + t) * CI + 8 * j);
-        const uint32_t a = sw0 + (uint32_t)((t * KB + (j >> 1)) * CO + o) * 32u + (uint32_t)(j & 1) * 16u;
+        const uint32_t a = sw0 + (uint32_t)(((dxi * KB + (j >> 1)) * 3 + bi) * CO + o) * 32u + (uint32_t)(j & 1) * 16u;
         asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(swz32(a)), "r"(v.x), "r"(v.y), "r"(v.z),
                      "r"(v.w)
                      : "memory");
@@ -283,6 +319,18 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *s_tmem;
+    // the accumulators start at zero (every MMA accumulates)
+    if (warp < FW_EPI_WARPS) {
+        const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        for (int r = warp >> 2; r < R; r += 2)
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c0 = 0; c0 < CO; c0 += 16) tmem_zero16(tq + (uint32_t)(b * ACC + r * CO + c0));
+        tmem_wait_st();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
 
     const int nrb = H / d / R, ncb = W / TC_COLS;
     const long long units = (long long)B * d * nrb * ncb;
@@ -290,7 +338,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     bool ok = true;
 
     if (warp == FW_TMA_WARP) {
-        // ---- TMA issuer: the unit's 128 columns of R + 2 rows, one box per row and plane
+        // ---- TMA issuer: the unit's 128 columns of R + 2 rows, one box per row
         if (lane == 0) {
             for (long long q = 0; q < mine * KB; ++q) {
                 const int s = (int)(q % S), kb = (int)(q % KB);
@@ -301,7 +349,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                 const uint32_t st = sin0 + (uint32_t)s * STAGE;
 #pragma unroll 1
                 for (int k = 0; k < R + 2; ++k)
-                    tma_load_3d(st + (uint32_t)(k * FW_PITCH + FW_HALO) * 32u, &xmap, 16 * kb, U.x0,
+                    tma_load_3d(st + (uint32_t)(k * PITCH + HALO) * 32u, &xmap, 16 * kb, U.x0,
                                 U.n * H + image_row(U, k, R, d, H), full(s));
             }
         }
@@ -317,13 +365,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             const int per_row = 2 * d * 2;  // 2d columns x two 16-byte halves of the plane
             for (int i = lane; i < (R + 2) * per_row; i += 32) {
                 const int k = i / per_row, rem = i % per_row, h = rem & 1, e = rem >> 1;  // e < 2d
-                // e < d: left column x0 - 1 - e (slot 7 - e); else right column x0 + 128 + (e - d)
+                // e < d: left column x0 - 1 - e (slot HALO - 1 - e); else right column x0 + 128 + (e - d)
                 int xx = e < d ? U.x0 - 1 - e : U.x0 + TC_COLS + (e - d);
-                const int slot = e < d ? FW_HALO - 1 - e : FW_HALO + TC_COLS + (e - d);
+                const int slot = e < d ? HALO - 1 - e : HALO + TC_COLS + (e - d);
                 xx += xx < 0 ? W : (xx >= W ? -W : 0);
                 const uint8_t* src = x + (((long long)U.n * H + image_row(U, k, R, d, H)) * W + xx) * (16LL * NC) +
                                      32 * kb + 16 * h;
-                const uint32_t dst = st + (uint32_t)(k * FW_PITCH + slot) * 32u + (uint32_t)h * 16u;
+                const uint32_t dst = st + (uint32_t)(k * PITCH + slot) * 32u + (uint32_t)h * 16u;
                 cp_async16(swz32(dst), src);
             }
             cp_async_commit();
@@ -331,10 +379,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             fence_proxy_async();
             mbar_arrive(full(s));
         }
-    } else if (warp == FW_MMA_WARP) {
-        // ---- MMA issuer
+    } else if (warp >= FW_MMA_WARP) {
+        // ---- MMA issuers: per plane, per input row k, per column tap dx
         if (lane == 0) {
-            for (long long j = 0; j < mine && ok; ++j) {
+            for (long long j = warp - FW_MMA_WARP; j < mine && ok; j += FW_MMA_WARPS) {
                 const int b = (int)(j & 1);
                 if (j >= 2) ok = mbar_wait(tempty(b), (uint32_t)(((j >> 1) - 1) & 1));
 #pragma unroll 1
@@ -346,14 +394,17 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     fence_after_sync();
                     const uint32_t sa = sin0 + (uint32_t)s * STAGE;
 #pragma unroll 1
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t dcol = tmem + (uint32_t)b * ACC + (uint32_t)r * CO;
+                    for (int k = 0; k < R + 2; ++k) {
+                        // output rows lo .. hi of the unit receive input row k (dy = k - 1 - i)
+                        const int lo = k - 2 > 0 ? k - 2 : 0, hi = k < R - 1 ? k : R - 1;
+                        const int n = (hi - lo + 1) * CO, bi = 2 - k + lo;
+                        const uint32_t idesc = idesc_bf16(128, n, 0, 0);
+                        const uint32_t dcol = tmem + (uint32_t)b * ACC + (uint32_t)(lo * CO);
 #pragma unroll
-                        for (int t = 0; t < 9; ++t) {
-                            const int dy = t / 3 - 1, dx = t % 3 - 1;
-                            const uint32_t aoff = (uint32_t)(((r + 1 + dy) * FW_PITCH + FW_HALO + dx * d) * 32);
-                            umma(dcol, sdesc_sw32(sa + aoff), sdesc_sw32(sw0 + (uint32_t)(t * KB + kb) * CO * 32u), IDESC,
-                                 (t | kb) != 0);
+                        for (int dxi = 0; dxi < 3; ++dxi) {
+                            const uint32_t aoff = (uint32_t)((k * PITCH + HALO + (dxi - 1) * d) * 32);
+                            umma(dcol, sdesc_sw32(sa + aoff),
+                                 sdesc_sw32(sw0 + (uint32_t)(((dxi * KB + kb) * 3 + bi) * CO) * 32u), idesc, 1u);
                         }
                     }
                     umma_commit(empty(s));
@@ -363,18 +414,21 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---- epilogue: TMEM lane quarter `warp`, pixel x0 + 32 warp + lane
+        // ---- epilogue: TMEM lane quarter warp % 4, pixel x0 + 32 (warp % 4) + lane,
+        // output rows r = warp / 4 (mod 2)
+        const int quarter = warp & 3;
+        const uint32_t stg = sstg + (uint32_t)warp * FW_STG;  // this warp's output staging row
         for (long long j = 0; j < mine; ++j) {
             const int b = (int)(j & 1);
             ok = mbar_wait(tfull(b), (uint32_t)((j >> 1) & 1));
             if (!ok) break;
             fence_after_sync();
             const Unit U = unit_of(blockIdx.x + j * gridDim.x, d, nrb, ncb);
-            const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)b * ACC;
+            const uint32_t tb = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * ACC;
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
+            for (int r = warp >> 2; r < R; r += 2) {
                 const int yy = U.rho + (U.rb * R + r) * d;
-                const long long px = ((long long)U.n * H + yy) * W + U.x0 + 32 * warp + lane;
+                const long long px = ((long long)U.n * H + yy) * W + U.x0 + 32 * quarter + lane;
                 if constexpr (CO == 48) {
                     float v[48];
                     tmem_ld48(tb + (uint32_t)(r * CO), v);
@@ -399,9 +453,24 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                             }
                         }
                     }
-                    uint4* yo = reinterpret_cast<uint4*>(static_cast<uint8_t*>(y) + px * CO * 2);
+                    // the previous TMA store from this staging row has read it
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                    __syncwarp();
 #pragma unroll
-                    for (int q4 = 0; q4 < 6; ++q4) yo[q4] = make_uint4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
+                    for (int q4 = 0; q4 < 6; ++q4)
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(stg + (uint32_t)(lane * 96 + 16 * q4)),
+                                     "r"(o[4 * q4]), "r"(o[4 * q4 + 1]), "r"(o[4 * q4 + 2]), "r"(o[4 * q4 + 3])
+                                     : "memory");
+                    fence_proxy_async();  // the staging row (generic stores) before the TMA reads it
+                    __syncwarp();
+                    if (lane == 0) {
+                        asm volatile(
+                            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                                reinterpret_cast<uint64_t>(&ymap)),
+                            "r"(0), "r"(U.x0 + 32 * quarter), "r"((int)(U.n * H + yy)), "r"(stg)
+                            : "memory");
+                        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                    }
                 } else {
                     static_assert(EPI == LBM_NN_RESIDUAL && CO == 16, "16-channel epilogue: residual");
                     float v[16];
@@ -415,10 +484,15 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                                             a.z + v[4 * q + 2] + s_bias[4 * q + 2], a.w + v[4 * q + 3] + s_bias[4 * q + 3]);
                     }
                 }
+#pragma unroll
+                for (int c0 = 0; c0 < CO; c0 += 16) tmem_zero16(tb + (uint32_t)(r * CO + c0));
             }
+            tmem_wait_st();
             fence_before_sync();
             mbar_arrive(tempty(b));
         }
+        // every TMA store of this warp complete before the CTA (and its staging) goes away
+        if (STAGED && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
     if (!ok) atomicOr(status, 1);
     cp_async_wait_all();
@@ -430,9 +504,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     }
 }
 
-template <int CI, int CO, int R, int S>
+template <int CI, int CO, int R, int S, int HALO>
 constexpr size_t conv_tc_smem() {
-    return (size_t)S * ((R + 2) * FW_PITCH * 32) + 9u * CI * CO * 2u + CO * 4 + (2 * S + 4) * 8 + 16;
+    return (size_t)S * ((R + 2) * (TC_COLS + 2 * HALO) * 32) + (CO == 48 ? FW_EPI_WARPS * FW_STG : 0) +
+           9u * CI * CO * 2u + CO * 4 + (2 * S + 4) * 8 + 16;
 }
 
 // Tensor map of an NHWC bfloat16 activation: {channel, x, image row}, boxes of
@@ -466,30 +541,47 @@ bool activation_map(CUtensorMap* map, const void* x, int C, int B, int H, int W)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int CI, int CO, int EPI, int R, int S>
+// Tensor map of a 48-channel NHWC bfloat16 output: boxes of all 48 channels x
+// 32 pixels x 1 row (one epilogue warp's staging row), no swizzle.
+bool output_map(CUtensorMap* map, void* y, int B, int H, int W) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {48, (cuuint64_t)W, (cuuint64_t)B * H};
+    const cuuint64_t strides[2] = {96, (cuuint64_t)W * 96};
+    const cuuint32_t box[3] = {48, 32, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int CI, int CO, int EPI, int R, int S, int HALO>
 int conv_tc_launch(const void* x, const void* w, const float* bias, void* y, const float* res, const void* mask, int B,
                    int H, int W, int d, int* status, cudaStream_t s) {
-    auto k = conv_tc_kernel<CI, CO, EPI, R, S>;
-    const size_t smem = std::max(conv_tc_smem<CI, CO, R, S>(), TC_MIN_SMEM);
-    static_assert(conv_tc_smem<CI, CO, R, S>() <= 227 * 1024, "shared memory");
-    CUtensorMap map;
+    auto k = conv_tc_kernel<CI, CO, EPI, R, S, HALO>;
+    const size_t smem = std::max(conv_tc_smem<CI, CO, R, S, HALO>(), TC_MIN_SMEM);
+    static_assert(conv_tc_smem<CI, CO, R, S, HALO>() <= 227 * 1024, "shared memory");
+    CUtensorMap map, ymap;
     if (!activation_map(&map, x, CI, B, H, W)) return LBM_ERR_CUDA;
+    if (CO == 48 ? !output_map(&ymap, y, B, H, W) : !activation_map(&ymap, x, CI, B, H, W)) return LBM_ERR_CUDA;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LBM_ERR_CUDA;
     const long long units = (long long)B * d * (H / d / R) * (W / TC_COLS);
     const int grid = (int)std::min<long long>(units, (long long)nn_sm_count());
-    k<<<grid, FW_THREADS, smem, s>>>(map, static_cast<const uint8_t*>(x), static_cast<const __nv_bfloat16*>(w), bias, y,
-                                     res, static_cast<const uint8_t*>(mask), B, H, W, d, status);
+    k<<<grid, FW_THREADS, smem, s>>>(map, ymap, static_cast<const uint8_t*>(x), static_cast<const __nv_bfloat16*>(w),
+                                     bias, y, res, static_cast<const uint8_t*>(mask), B, H, W, d, status);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-// Rows per unit and stages (one 16-channel plane of a unit each): 4 rows and 6
-// stages where the rows divide, else 1 row and 12 stages (166 KB either way).
+// Rows per unit, stages (one 16-channel plane of a unit each) and halo slots:
+// 4 rows, 6 stages, 4 halo slots for dilations up to 4 where the rows divide by
+// 4; else 1 row, 6 stages, 8 slots.
 template <int CI, int CO, int EPI>
 int conv_tc_dispatch(const void* x, const void* w, const float* bias, void* y, const float* res, const void* mask,
                      int B, int H, int W, int d, int* status, cudaStream_t s) {
-    if ((H / d) % 4 == 0) return conv_tc_launch<CI, CO, EPI, 4, 6>(x, w, bias, y, res, mask, B, H, W, d, status, s);
-    return conv_tc_launch<CI, CO, EPI, 1, 12>(x, w, bias, y, res, mask, B, H, W, d, status, s);
+    if ((H / d) % 4 == 0 && d <= 4)
+        return conv_tc_launch<CI, CO, EPI, 4, 6, 4>(x, w, bias, y, res, mask, B, H, W, d, status, s);
+    return conv_tc_launch<CI, CO, EPI, 1, 6, 8>(x, w, bias, y, res, mask, B, H, W, d, status, s);
 }
 
 // ------------------------------------------------------ weight gradient --
@@ -509,14 +601,14 @@ int conv_tc_dispatch(const void* x, const void* w, const float* bias, void* y, c
 // Bytes the M = 64 side reads past the end of a stage: its fourth plane (rows 48..63
 // of M: read by the tensor cores, never used).
 __host__ __device__ constexpr uint32_t wgrad_slack(int CI, int CO, int R) {
-    const uint32_t psx = (uint32_t)((R + 2) * FW_PITCH * 32), psd = (uint32_t)(R * TC_COLS * 32);
+    const uint32_t psx = (uint32_t)((R + 2) * WG_PITCH * 32), psd = (uint32_t)(R * TC_COLS * 32);
     const uint32_t stage = (uint32_t)(CI / 16) * psx + (uint32_t)(CO / 16) * psd;
     const uint32_t a_end = CI >= CO ? 4 * psx : (uint32_t)(CI / 16) * psx + 4 * psd;
     return a_end > stage ? a_end - stage : 0u;
 }
 
 template <int CI, int CO, int R, int S>
-__global__ void __launch_bounds__(FW_THREADS, 1)
+__global__ void __launch_bounds__(WG_THREADS, 1)
     wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dmap,
                     const uint8_t* __restrict__ x, float* __restrict__ partials, int B, int H, int W, int d,
                     int* __restrict__ status) {
@@ -527,13 +619,13 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     constexpr int MREAL = A_IS_X ? CI : CO;            // real rows of M = 64
     constexpr uint32_t TCOLS = pow2_cols(9 * N);
     constexpr uint32_t IDESC = idesc_bf16(64, N, 1, 1);
-    constexpr uint32_t PSX = (uint32_t)((R + 2) * FW_PITCH * 32);  // x plane: R + 2 rows with halo slots
+    constexpr uint32_t PSX = (uint32_t)((R + 2) * WG_PITCH * 32);  // x plane: R + 2 rows with halo slots
     constexpr uint32_t PSD = (uint32_t)(R * TC_COLS * 32);         // dy plane: R rows of 128 pixels
     constexpr uint32_t STAGE = KX * PSX + KD * PSD;
     constexpr uint32_t TX = (uint32_t)((R + 2) * KX + R * KD) * TC_COLS * 32;
     constexpr int HW = S;  // halo warps in use: one per stage
     static_assert(MREAL <= 64 && N % 16 == 0, "M = 64 UMMA shapes");
-    static_assert(S <= FW_HALO_WARPS, "one halo warp per stage");
+    static_assert(S <= WG_HALO_WARPS, "one halo warp per stage");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sin0 = smem_u32(smem);
@@ -552,7 +644,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
         mbar_init_n(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == FW_MMA_WARP) tmem_alloc(smem_u32(s_tmem), TCOLS);
+    if (warp == WG_MMA_WARP) tmem_alloc(smem_u32(s_tmem), TCOLS);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -562,7 +654,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     const long long mine = units > blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     bool ok = true;
 
-    if (warp == FW_TMA_WARP) {
+    if (warp == WG_TMA_WARP) {
         if (lane == 0) {
             for (long long j = 0; j < mine; ++j) {
                 const int s = (int)(j % S);
@@ -576,7 +668,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                     const int row = U.n * H + image_row(U, k, R, d, H);
 #pragma unroll
                     for (int kb = 0; kb < KX; ++kb)
-                        tma_load_3d(st + (uint32_t)kb * PSX + (uint32_t)(k * FW_PITCH + FW_HALO) * 32u, &xmap, 16 * kb,
+                        tma_load_3d(st + (uint32_t)kb * PSX + (uint32_t)(k * WG_PITCH + WG_HALO) * 32u, &xmap, 16 * kb,
                                     U.x0, row, full(s));
                     if (k >= 1 && k <= R) {
 #pragma unroll
@@ -588,10 +680,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             }
         }
         __syncwarp();
-    } else if (warp >= FW_HALO_WARP && warp < FW_HALO_WARP + HW) {
+    } else if (warp >= WG_HALO_WARP && warp < WG_HALO_WARP + HW) {
         // halo warp h serves stage h only, so it waits on every phase of that
         // stage's barrier in order (a parity wait cannot tell phases two apart)
-        for (long long j = warp - FW_HALO_WARP; j < mine; j += HW) {
+        for (long long j = warp - WG_HALO_WARP; j < mine; j += HW) {
             const int s = (int)(j % S);
             if (j >= S) ok = mbar_wait(empty(s), (uint32_t)(((j / S) - 1) & 1));
             if (!ok) break;
@@ -601,10 +693,10 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             for (int i = lane; i < (R + 2) * per_row; i += 32) {
                 const int k = i / per_row, rem = i % per_row, jc = rem % NCX, e = rem / NCX;
                 int xx = e < d ? U.x0 - 1 - e : U.x0 + TC_COLS + (e - d);
-                const int slot = e < d ? FW_HALO - 1 - e : FW_HALO + TC_COLS + (e - d);
+                const int slot = e < d ? WG_HALO - 1 - e : WG_HALO + TC_COLS + (e - d);
                 xx += xx < 0 ? W : (xx >= W ? -W : 0);
                 const uint8_t* src = x + (((long long)U.n * H + image_row(U, k, R, d, H)) * W + xx) * (16LL * NCX) + 16 * jc;
-                const uint32_t dst = st + (uint32_t)(jc >> 1) * PSX + (uint32_t)(k * FW_PITCH + slot) * 32u +
+                const uint32_t dst = st + (uint32_t)(jc >> 1) * PSX + (uint32_t)(k * WG_PITCH + slot) * 32u +
                                      (uint32_t)(jc & 1) * 16u;
                 cp_async16(swz32(dst), src);
             }
@@ -613,7 +705,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
             fence_proxy_async();
             mbar_arrive(full(s));
         }
-    } else if (warp == FW_MMA_WARP) {
+    } else if (warp == WG_MMA_WARP) {
         if (lane == 0) {
             for (long long j = 0; j < mine; ++j) {
                 const int s = (int)(j % S);
@@ -631,7 +723,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
                         for (int t = 0; t < 9; ++t) {
                             const int dy = t / 3 - 1, dx = t % 3 - 1;
                             const uint64_t xd =
-                                sdesc(sx + (uint32_t)((r + 1 + dy) * FW_PITCH + FW_HALO + dx * d + p0) * 32u, PSX, 256) |
+                                sdesc(sx + (uint32_t)((r + 1 + dy) * WG_PITCH + WG_HALO + dx * d + p0) * 32u, PSX, 256) |
                                 ((uint64_t)LAYOUT_SW32 << 61);
                             const uint32_t first = (j == 0 && r == 0 && p0 == 0);
                             umma(tmem + (uint32_t)(t * N), A_IS_X ? xd : dd, A_IS_X ? dd : xd, IDESC, !first);
@@ -671,7 +763,7 @@ __global__ void __launch_bounds__(FW_THREADS, 1)
     cp_async_wait_all();
     fence_before_sync();
     __syncthreads();
-    if (warp == FW_MMA_WARP) {
+    if (warp == WG_MMA_WARP) {
         fence_after_sync();
         tmem_free(tmem, TCOLS);
     }
@@ -690,7 +782,7 @@ __global__ void wgrad_tc_reduce(const float* __restrict__ partials, int nb, int 
 
 template <int CI, int CO, int R, int S>
 constexpr size_t wgrad_tc_smem() {
-    return (size_t)S * ((CI / 16) * (R + 2) * FW_PITCH * 32 + (CO / 16) * R * TC_COLS * 32) +
+    return (size_t)S * ((CI / 16) * (R + 2) * WG_PITCH * 32 + (CO / 16) * R * TC_COLS * 32) +
            wgrad_slack(CI, CO, R) + (2 * S + 1) * 8 + 16;
 }
 
@@ -710,7 +802,7 @@ int wgrad_tc_launch(const void* x, const void* dy, float* dw, float* part, int B
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LBM_ERR_CUDA;
     const int grid = (int)std::min<long long>(wgrad_units(B, H, W, d, R), (long long)nn_sm_count());
-    k<<<grid, FW_THREADS, smem, s>>>(xmap, dmap, static_cast<const uint8_t*>(x), part, B, H, W, d, status);
+    k<<<grid, WG_THREADS, smem, s>>>(xmap, dmap, static_cast<const uint8_t*>(x), part, B, H, W, d, status);
     wgrad_tc_reduce<<<64, 256, 0, s>>>(part, grid, CO, CI, dw);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
