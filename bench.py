@@ -178,9 +178,11 @@ def make_workload(name, cells_cap=None):
     return wl.droplets8192(nx=int(nx * s), ny=int(ny * s))
 
 
-def oracle_mlups(name, steps_budget_s, cells_cap, min_steps=2):
-    """Time the FP64 CPU oracle (one thread) on a bounded sample of the workload."""
+def oracle_mlups(name, steps_budget_s, cells_cap, min_steps=2, threads=1):
+    """Time the FP64 CPU oracle on a bounded sample of the workload with
+    `threads` host threads (its per-node loops; results do not depend on it)."""
     import oracle
+    oracle.set_threads(threads)
     w = make_workload(name, cells_cap)
     s = oracle.OracleSim(w.params)
     s.init(w.sdf, w.c1_tilde, w.c2_tilde)
@@ -191,7 +193,26 @@ def oracle_mlups(name, steps_budget_s, cells_cap, min_steps=2):
     t = time.perf_counter()
     s.step(steps)
     dt = time.perf_counter() - t
+    oracle.set_threads(1)
     return w.cells * steps / dt / 1e6, w, steps, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(name, cells_cap, what):
+    """The oracle on all host cores (the baseline value) and on one thread."""
+    cores = host_cores()
+    mlups, sw, steps, dt = oracle_mlups(name, 10.0, cells_cap, threads=cores)
+    one, _, steps1, dt1 = oracle_mlups(name, 10.0, cells_cap, threads=1)
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "single_thread_value": one,
+            "sample": "%s %dx%d, FP64: %d steps in %.1f s on %d threads; %d steps in %.1f s on one" % (
+                what, sw.params["nx"], sw.params["ny"], steps, dt, cores, steps1, dt1)}
 
 
 def run_reference(args, rank, world):
@@ -199,6 +220,8 @@ def run_reference(args, rank, world):
     if world > 1 and rank != 0:
         return
     import oracle
+    cores = host_cores()
+    oracle.set_threads(cores)
     full = make_workload(args.workload)
     # each step a bounded sample so that warmup + steps end within ~2-3 minutes
     per_step_cells = int(max(4096, min(full.cells, 0.6e6 * 150.0 / max(1, args.steps + args.warmup))))
@@ -219,7 +242,7 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": args.workload, "nx": full.params["nx"], "ny": full.params["ny"],
                    "sample_nx": w.params["nx"], "sample_ny": w.params["ny"]},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -318,10 +341,7 @@ def run_ours(args, rank, world, local):
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, sw, steps, dt = oracle_mlups(args.workload, 15.0, 256 * 512)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": "%s scaled to %dx%d, %d steps, %.1f s, FP64, one thread" % (
-                   args.workload, sw.params["nx"], sw.params["ny"], steps, dt)}
+        cpu = cpu_baseline(args.workload, 256 * 512, args.workload + " scaled to")
 
     if rank == 0:
         line = {
@@ -449,10 +469,7 @@ def run_batched(args, rank, world, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, sw, steps, dt = oracle_mlups(args.workload, 15.0, 64 * 64)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": "one %dx%d case of the batch, %d steps, %.1f s, FP64, one thread" % (
-                   sw.params["nx"], sw.params["ny"], steps, dt)}
+        cpu = cpu_baseline(args.workload, 64 * 64, "one case of the batch,")
 
     if rank == 0:
         graphs, rest = divmod(args.steps, 32)

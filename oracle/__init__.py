@@ -44,14 +44,16 @@ class OrcParams(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (plain C11, FP64, no FMA contraction)."""
+    """Compile oracle.c into liboracle.so (plain C11, FP64, no FMA contraction;
+    OpenMP for the per-node loops when the compiler has it, else serial)."""
     srcs = (_SRC, os.path.join(_HERE, "oracle.h"))
     if not force and os.path.exists(_LIB) and all(
             os.path.getmtime(_LIB) >= os.path.getmtime(s) for s in srcs):
         return _LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", _LIB + ".tmp", _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+            "-o", _LIB + ".tmp", _SRC, "-lm"]
+    if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
@@ -78,8 +80,19 @@ def lib() -> ctypes.CDLL:
         L.orc_taus.argtypes = [ctypes.c_void_p, dp]
         L.orc_cell_functions.argtypes = [ctypes.POINTER(OrcParams), dp, dp]
         L.orc_solve_scalars.argtypes = [ctypes.POINTER(OrcParams), dp, dp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_threads.restype = ctypes.c_int
         _lib = L
+        set_threads(1)  # serial unless a caller asks for more
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's per-node loops (results do not depend on
+    it); returns the number now in use (1 without OpenMP)."""
+    L = lib()
+    L.orc_set_threads(int(n))
+    return int(L.orc_threads())
 
 
 DEFAULTS = dict(wall_x=0, wall_y=0, scalar_q=5, W=4.0, M=0.01, sigma=0.0,

@@ -2,8 +2,12 @@
  * FP64 CPU oracle: the paper's lattice Boltzmann time step written out plainly.
  *
  * TEST INFRASTRUCTURE ONLY (see oracle.h).  Slow on purpose: one pass per
- * stage of the algorithm, per-cell loops, push streaming, FP64 throughout,
- * single thread.  It shares nothing with the CUDA library.
+ * stage of the algorithm, per-cell loops, push streaming, FP64 throughout.
+ * The per-node loops of a stage may run on several host threads (OpenMP, when
+ * the build has it; orc_set_threads): every node writes only its own outputs
+ * and the arithmetic of a node does not depend on the thread count, so results
+ * are bit-identical to one thread.  Sums (orc_conserved) stay serial.  It
+ * shares nothing with the CUDA library.
  *
  * Paper: B. Chen, C. Zhan, Z. Chai, B. Shi, "A phase-field-based lattice
  * Boltzmann method for two-phase flows with the interfacial mass/heat
@@ -37,6 +41,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- lattice (Sec. IV: D2Q9 in two dimensions; D2Q5 option for scalars) ---- */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -249,6 +256,7 @@ static double laplacian(const orc_sim* s, const double* fld, int x, int y) {
 /* ---- stage 1: zeroth moments phi (Eq. 26) and c1, c2 (Eq. 37) ---- */
 static void zeroth_moments(orc_sim* s) {
     const int N = s->N, qs = s->p.scalar_q;
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < N; ++k) {
         double phi = 0.0, P1 = 0.0, P2 = 0.0;
         for (int i = 0; i < 9; ++i) phi += s->f[i * N + k];
@@ -455,6 +463,8 @@ static void collide_cell(orc_sim* s, int x, int y) {
 static void stream_lattice(orc_sim* s, const double* post, double* dst, int q) {
     const orc_params* p = &s->p;
     const int N = s->N;
+    /* every (direction, destination) entry is written by exactly one source node */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
         for (int x = 0; x < p->nx; ++x) {
             const int k = y * p->nx + x;
@@ -615,6 +625,7 @@ void orc_step(orc_sim* s, long nsteps) {
     const int N = s->N;
     for (long n = 0; n < nsteps; ++n) {
         zeroth_moments(s);
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) collide_cell(s, x, y);
         /* the previous-step macros are replaced only after every cell has collided */
@@ -684,6 +695,22 @@ void orc_conserved(orc_sim* s, double out[2]) {
     }
     out[0] = a;
     out[1] = b;
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n < 1 ? 1 : n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void orc_taus(const orc_sim* s, double out[3]) {

@@ -67,6 +67,10 @@ void     orc_get_fields(orc_sim* s, double* out);
 void     orc_get_stencils(orc_sim* s, double* out);
 /* {sum phi, sum (c1 + c2)} of the current state. */
 void     orc_conserved(orc_sim* s, double out[2]);
+/* Host threads of the per-node loops (1 = serial; results do not depend on it).
+ * orc_threads() reports the current number (1 in a build without OpenMP). */
+void     orc_set_threads(int n);
+int      orc_threads(void);
 /* Relaxation times {tau_f, tau_h1, tau_h2}. */
 void     orc_taus(const orc_sim* s, double out[3]);
 

@@ -517,3 +517,28 @@ def test_planar_interface_erfc_with_local_gradients(scheme):
             exact = 1 / (K + r) * erfc((i - x0) / (2 * sqrt(D2 * steps)))
             errs.append(abs(c2[i] / (1 - phi[i]) - exact))
     assert max(errs) < 0.02, max(errs)
+
+
+# ------------------------------------------------------ host threads --
+def test_oracle_threads_give_bit_identical_states():
+    """The oracle's per-node loops may run on several host threads; every node
+    writes only its own outputs, so the state after many steps is bit-identical
+    to the serial run (wall-bounded bubble at density ratio 1000, D2Q9 scalars
+    with Eq. (48) viscosity on a ragged periodic grid)."""
+    import os
+    cases = [(wl.bubble1024x2048(nx=48, ny=96).params, wl.bubble1024x2048(nx=48, ny=96), 60),
+             (dict(wl.droplet64(nx=37, ny=23, R=7.0, scalar_q=9, visc_model=1, rho2=0.2).params),
+              wl.droplet64(nx=37, ny=23, R=7.0), 60)]
+    try:
+        for params, w, steps in cases:
+            got = []
+            for n in (1, max(2, os.cpu_count() or 2)):
+                oracle.set_threads(n)
+                s = oracle.OracleSim(params)
+                s.init(w.sdf, w.c1_tilde, w.c2_tilde)
+                s.step(steps)
+                got.append(s.fields())
+            for k in got[0]:
+                assert np.array_equal(got[0][k], got[1][k]), k
+    finally:
+        oracle.set_threads(1)
