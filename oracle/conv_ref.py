@@ -87,6 +87,42 @@ def net_loss_and_grads(x, target, weights, biases, used=5, dil=(1,) * 6):
     return loss, gw, gb
 
 
+def _backward(x, acts, dz, weights, dil):
+    """Weight and bias gradients of one network application from the gradient
+    dz at its output, and the gradient at its input (residual path plus layer
+    0's adjoint)."""
+    gw, gb = [None] * 6, [None] * 6
+    dout = dz
+    for l in range(5, -1, -1):
+        gw[l] = conv3x3_wgrad(acts[l], dz, dil[l])
+        gb[l] = dz.sum(axis=(0, 1, 2))
+        if l > 0:
+            dz = conv3x3_dgrad(dz, weights[l], dil[l]) * (acts[l] > 0.0)
+        else:
+            dz = conv3x3_dgrad(dz, weights[0], dil[0])
+    return gw, gb, dout + dz
+
+
+def net_two_hop_loss_and_grads(x, t1, t2, weights, biases, used=5, dil=(1,) * 6):
+    """Loss of two hops unrolled through the network, MSE(net(x), t1) +
+    MSE(net(net(x)), t2), and its gradients with respect to every weight and
+    bias (the second hop's input gradient flows into the first hop's output)."""
+    acts1, out1 = net_forward(x, weights, biases, dil)
+    acts2, out2 = net_forward(out1, weights, biases, dil)
+    npx = out1.shape[0] * out1.shape[1] * out1.shape[2]
+
+    def mse(out, t):
+        d = np.zeros_like(out)
+        d[..., :used] = out[..., :used] - np.asarray(t, dtype=np.float64)[..., :used]
+        return float((d ** 2).sum() / (npx * used)), 2.0 * d / (npx * used)
+
+    l1, d1 = mse(out1, t1)
+    l2, d2 = mse(out2, t2)
+    gw2, gb2, dx2 = _backward(out1, acts2, d2, weights, dil)
+    gw1, gb1, _ = _backward(x, acts1, d1 + dx2, weights, dil)
+    return l1 + l2, [a + b for a, b in zip(gw1, gw2)], [a + b for a, b in zip(gb1, gb2)]
+
+
 def adam(param, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One bias-corrected Adam step (Kingma & Ba 2015), float64."""
     m = beta1 * m + (1.0 - beta1) * grad

@@ -106,6 +106,41 @@ def test_network_gradients_match_finite_differences(dil):
     assert loss > 0
 
 
+def test_two_hop_gradients_match_finite_differences():
+    """The unrolled two-hop loss (the second hop from the network's own first
+    hop) against central differences of itself, weights and biases of every
+    layer, with dilated layers."""
+    dil = (1, 2, 1, 2, 1, 1)
+    x, t1, weights, biases = _net(8, h=6, w=8)
+    t2 = np.zeros_like(x)
+    t2[..., :5] = np.random.default_rng(9).standard_normal(x[..., :5].shape)
+    loss, gw, gb = cr.net_two_hop_loss_and_grads(x, t1, t2, weights, biases, dil=dil)
+    g = np.random.default_rng(10)
+    eps = 1e-6
+    f = lambda w_, b_: cr.net_two_hop_loss_and_grads(x, t1, t2, w_, b_, dil=dil)[0]
+    for _ in range(16):
+        l = int(g.integers(0, 6))
+        co, ci = cr.LAYERS[l][1], cr.LAYERS[l][0]
+        o = int(g.integers(0, 5 if l == 5 else co))
+        if g.random() < 0.75:
+            c = int(g.integers(0, 5 if l == 0 else ci))
+            t = int(g.integers(0, 9))
+            wp = [v.copy() for v in weights]
+            wm = [v.copy() for v in weights]
+            wp[l][o, t, c] += eps
+            wm[l][o, t, c] -= eps
+            assert gw[l][o, t, c] == pytest.approx((f(wp, biases) - f(wm, biases)) / (2 * eps), rel=1e-5, abs=1e-9)
+        else:
+            bp = [v.copy() for v in biases]
+            bm = [v.copy() for v in biases]
+            bp[l][o] += eps
+            bm[l][o] -= eps
+            assert gb[l][o] == pytest.approx((f(weights, bp) - f(weights, bm)) / (2 * eps), rel=1e-5, abs=1e-9)
+    # the one-hop part alone is the one-hop reference
+    l1 = cr.net_loss_and_grads(x, t1, weights, biases, dil=dil)[0]
+    assert 0 < l1 < loss
+
+
 def test_adam_first_step_is_lr_times_the_gradient_sign():
     g = np.array([3.0, -0.5, 1e-3, -20.0])
     p1, m, v = cr.adam(np.zeros(4), g, np.zeros(4), np.zeros(4), t=1, lr=0.01, eps=0.0)
