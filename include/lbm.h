@@ -186,9 +186,10 @@ int lbm_conserved(lbm_handle* h, double out[2]);
 int lbm_sync(lbm_handle* h);
 
 /* Checkpoint: the populations and previous-step macros of the current state.
- * lbm_state_bytes gives the size; get/set copy to/from caller memory (host or
- * device) and synchronise.  Restoring then stepping is bit-identical to never
- * having stopped. */
+ * lbm_state_bytes gives the size; get/set copy to/from caller memory: a host
+ * buffer synchronises the stream, a device buffer (on_device != 0) is copied
+ * asynchronously on the handle's stream.  Restoring then stepping is
+ * bit-identical to never having stopped. */
 size_t lbm_state_bytes(const lbm_handle* h);
 int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device);
 int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_device);
@@ -290,6 +291,31 @@ int lbm_batch_autotune(lbm_batch* b, int32_t steps_per_trial, double* table, int
  * up (default 2^21, about a second) and a tile whose completion is never
  * published (-1: none). */
 int lbm_batch_set_wait_limit(lbm_batch* b, int64_t spin_limit, int32_t hold_tile);
+
+/* Restart every case at the equilibria of its six macroscopic fields, as
+ * lbm_init_macros does case by case.  macros: the cases' fields concatenated in
+ * the batch's case order, each case as six (ny, nx) row-major FP64 arrays
+ * {phi, ux, uy, p, c1, c2} (6 * nx * ny doubles per case), on the host or, with
+ * on_device != 0, in device memory (asynchronous on the stream).  The batch
+ * notices the restart at its next step.  An error names the failing case; the
+ * cases before it have been restarted. */
+int lbm_batch_init_macros(lbm_batch* b, const double* macros, int32_t on_device);
+
+/* lbm_get_fields of every case into one buffer: case by case, in the batch's
+ * order, the selected fields (k of them, in LBM_FIELD bit order) as k (ny, nx)
+ * row-major arrays of out_dtype.  Device output is asynchronous on the stream;
+ * host output synchronises. */
+int lbm_batch_get_fields(lbm_batch* b, uint32_t mask, void* out, int32_t out_on_device,
+                         int32_t out_dtype);
+
+/* Checkpoint of every case: lbm_get_state / lbm_set_state of each case into or
+ * out of consecutive slices of one buffer of lbm_batch_state_bytes bytes
+ * (case i's slice starts at the sum of the earlier cases' lbm_state_bytes).  A
+ * device buffer is copied asynchronously on the stream; a host buffer
+ * synchronises.  After set_state every case's step count restarts at 0. */
+size_t lbm_batch_state_bytes(const lbm_batch* b);
+int lbm_batch_get_state(lbm_batch* b, void* buf, size_t bytes, int32_t on_device);
+int lbm_batch_set_state(lbm_batch* b, const void* buf, size_t bytes, int32_t on_device);
 
 /* Release the batch (and its graph); workspace and cases stay the caller's. */
 void lbm_batch_destroy(lbm_batch* b);

@@ -12,7 +12,7 @@ import hashlib
 import json
 import os
 
-from .lbm import LBM_OK, LBMError, Simulation, load_library
+from .lbm import FIELD_BITS, FIELDS, LBM_OK, LBM_OUT_F32, LBM_OUT_F64, LBMError, Simulation, load_library
 
 
 def _check(L, b, rc):
@@ -29,6 +29,7 @@ class Batch:
 
     def __init__(self, sims: list[Simulation]):
         import torch
+        self._torch = torch
         self.L = load_library()
         self.sims = list(sims)
         n = len(self.sims)
@@ -65,6 +66,46 @@ class Batch:
 
     def sync(self):
         _check(self.L, self._b, self.L.lbm_batch_sync(self._b))
+
+    def init_macros(self, macros):
+        """Restart every case at the equilibria of its fields: `macros` is a
+        contiguous FP64 device tensor holding, case after case, the six (ny, nx)
+        fields phi, ux, uy, p, c1, c2 (shape [B, 6, ny, nx] when all cases share
+        a shape).  Asynchronous on the stream."""
+        assert macros.is_cuda and macros.dtype == self._torch.float64 and macros.is_contiguous()
+        assert macros.numel() == 6 * self.cells
+        _check(self.L, self._b, self.L.lbm_batch_init_macros(self._b, macros.data_ptr(), 1))
+
+    def fields(self, names, out):
+        """The selected fields of every case into the contiguous FP32 or FP64
+        device tensor `out` (case after case, fields in the library's order;
+        shape [B, k, ny, nx] when all cases share a shape).  Asynchronous."""
+        names = [n for n in FIELDS if n in names]
+        mask = 0
+        for n in names:
+            mask |= FIELD_BITS[n]
+        t = self._torch
+        assert out.is_cuda and out.is_contiguous() and out.numel() == len(names) * self.cells
+        code = LBM_OUT_F64 if out.dtype == t.float64 else LBM_OUT_F32
+        assert out.dtype in (t.float64, t.float32)
+        _check(self.L, self._b, self.L.lbm_batch_get_fields(self._b, mask, out.data_ptr(), 1, code))
+        return out
+
+    def state_bytes(self) -> int:
+        return int(self.L.lbm_batch_state_bytes(self._b))
+
+    def get_state(self, out=None):
+        """Every case's checkpoint into one device buffer (uint8, allocated when
+        `out` is None).  Asynchronous on the stream."""
+        n = self.state_bytes()
+        if out is None:
+            out = self._torch.empty(n, dtype=self._torch.uint8, device=self.sims[0].device)
+        _check(self.L, self._b, self.L.lbm_batch_get_state(self._b, out.data_ptr(), out.numel(), 1))
+        return out
+
+    def set_state(self, buf):
+        """Restore every case from a buffer written by get_state (asynchronous)."""
+        _check(self.L, self._b, self.L.lbm_batch_set_state(self._b, buf.data_ptr(), buf.numel(), 1))
 
     def set_tiling(self, tile_w: int, tile_h: int):
         _check(self.L, self._b, self.L.lbm_batch_set_tiling(self._b, int(tile_w), int(tile_h)))

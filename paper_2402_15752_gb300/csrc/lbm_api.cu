@@ -277,6 +277,7 @@ int lbm_init_macros(lbm_handle* h, const double* phi, const double* ux, const do
 }
 
 int lbm_step(lbm_handle* h, int64_t nsteps) {
+    const lbm::NvtxRange range("lbm_step");
     if (!h) return LBM_ERR_ARG;
     if (nsteps < 0) return h->fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (h->nonfinite_seen()) return h->fail(LBM_ERR_NONFINITE, "a previous step produced a non-finite macro value");
@@ -305,6 +306,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 }
 
 int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_device, int32_t out_dtype) {
+    const lbm::NvtxRange range("lbm_get_fields");
     if (!h) return LBM_ERR_ARG;
     mask &= LBM_FIELD_ALL;
     if (!mask || !out) return h->fail(LBM_ERR_ARG, "empty field mask or NULL output");
@@ -351,6 +353,7 @@ int lbm_sync(lbm_handle* h) {
 }
 
 int lbm_conserved(lbm_handle* h, double out[2]) {
+    const lbm::NvtxRange range("lbm_conserved");
     if (!h) return LBM_ERR_ARG;
     if (!out) return h->fail(LBM_ERR_ARG, "out is NULL");
     DeviceGuard dg(h->device);
@@ -380,7 +383,7 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device) {
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaMemcpyAsync(buf, h->pop(h->cur), a, k, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<uint8_t*>(buf) + a, h->prev(), b, k, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_state", e);
     return LBM_OK;
 }
@@ -394,7 +397,7 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_devic
     cudaError_t e = cudaMemcpyAsync(h->pop(0), buf, a, k, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->prev(), static_cast<const uint8_t*>(buf) + a, b, k, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_set_state", e);
     h->cur = 0;
     h->t = 0;

@@ -102,6 +102,11 @@ struct lbm_batch {
     bool failed = false;        // a wait gave up: the lattices are out of step
     cudaGraphExec_t graph = nullptr;
     bool graph_tried = false;
+    // pinned staging of the case descriptors; the event marks the end of the
+    // last copy out of it, so a reset rewrites it only once that copy is done
+    lbm::BatchCase* h_cases = nullptr;
+    cudaEvent_t cases_ev = nullptr;
+    bool cases_ev_live = false;
     char err[512] = "";
 
     lbm::BatchCase* d_cases() const { return reinterpret_cast<lbm::BatchCase*>(ws + L.off_cases); }
@@ -138,9 +143,14 @@ struct lbm_batch {
     }
 
     // Case descriptors with each lattice's current buffer, step counters and
-    // status word zeroed (stream-ordered after everything already queued).
+    // status word zeroed (stream-ordered after everything already queued; the
+    // host does not wait for the stream).
     cudaError_t reset_counters() {
-        std::vector<lbm::BatchCase> hc(cases.size());
+        if (cases_ev_live) {
+            const cudaError_t w = cudaEventSynchronize(cases_ev);
+            if (w != cudaSuccess) return w;
+        }
+        lbm::BatchCase* hc = h_cases;
         cur0.resize(cases.size());
         for (size_t i = 0; i < cases.size(); ++i) {
             lbm_handle* h = cases[i];
@@ -155,11 +165,12 @@ struct lbm_batch {
             c.cur0 = h->cur;
             cur0[i] = h->cur;
         }
-        cudaError_t e = cudaMemcpyAsync(d_cases(), hc.data(), hc.size() * sizeof(lbm::BatchCase),
+        cudaError_t e = cudaMemcpyAsync(d_cases(), hc, cases.size() * sizeof(lbm::BatchCase),
                                         cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(cases_ev, stream);
+        cases_ev_live = e == cudaSuccess;
         if (e == cudaSuccess) e = cudaMemsetAsync(d_done(), 0, (size_t)tiles_cap * sizeof(unsigned), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_status(), 0, BALIGN, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // hc is pageable
         steps = 0;
         failed = false;
         return e;
@@ -321,10 +332,12 @@ int lbm_batch_create(lbm_handle* const* cases, int32_t ncases, void* d_workspace
     b->L = L;
     b->tiles_cap = cap;
     lbm::detail::DeviceGuard dg(b->device);
-    rc = build_tiling(b, 128, 16);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&b->h_cases), (size_t)ncases * sizeof(lbm::BatchCase));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cases_ev, cudaEventDisableTiming);
+    rc = e == cudaSuccess ? build_tiling(b, 128, 16) : b->fail(LBM_ERR_CUDA, "lbm_batch_create: staging", e);
     if (rc != LBM_OK) {
         snprintf(g_batch_error, sizeof(g_batch_error), "%s", b->err);
-        delete b;
+        lbm_batch_destroy(b);
         return rc;
     }
     *out = b;
@@ -347,6 +360,7 @@ int lbm_batch_tiling(const lbm_batch* b, int32_t* tile_w, int32_t* tile_h, int32
 }
 
 int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    const lbm::NvtxRange range("lbm_batch_step");
     if (!b) return LBM_ERR_ARG;
     if (nsteps < 0) return b->fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (b->failed) return b->fail(LBM_ERR_TIMEOUT, "an earlier batched launch gave up waiting; set the tiling again after re-initialising the cases");
@@ -464,7 +478,86 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     lbm::detail::DeviceGuard dg(b->device);
     b->drop_graph();
+    if (b->cases_ev) {
+        if (b->cases_ev_live) cudaEventSynchronize(b->cases_ev);
+        cudaEventDestroy(b->cases_ev);
+    }
+    if (b->h_cases) cudaFreeHost(b->h_cases);
     delete b;
+}
+
+int lbm_batch_init_macros(lbm_batch* b, const double* macros, int32_t on_device) {
+    const lbm::NvtxRange range("lbm_batch_init_macros");
+    if (!b) return LBM_ERR_ARG;
+    if (!macros) return b->fail(LBM_ERR_ARG, "macros is NULL");
+    size_t off = 0;
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+        lbm_handle* h = b->cases[i];
+        const size_t n = (size_t)h->p.nx * h->p.ny;
+        const double* m = macros + off;
+        const int rc = lbm_init_macros(h, m, m + n, m + 2 * n, m + 3 * n, m + 4 * n, m + 5 * n, on_device);
+        if (rc != LBM_OK) {
+            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+            return rc;
+        }
+        off += 6 * n;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_fields(lbm_batch* b, uint32_t mask, void* out, int32_t out_on_device, int32_t out_dtype) {
+    const lbm::NvtxRange range("lbm_batch_get_fields");
+    if (!b) return LBM_ERR_ARG;
+    mask &= LBM_FIELD_ALL;
+    if (!mask || !out) return b->fail(LBM_ERR_ARG, "empty field mask or NULL output");
+    if (out_dtype != LBM_OUT_F64 && out_dtype != LBM_OUT_F32) return b->fail(LBM_ERR_ARG, "out_dtype must be LBM_OUT_F64 or LBM_OUT_F32");
+    const size_t es = out_dtype == LBM_OUT_F64 ? sizeof(double) : sizeof(float);
+    int k = 0;
+    for (uint32_t m = mask; m; m &= m - 1) ++k;
+    size_t off = 0;
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+        lbm_handle* h = b->cases[i];
+        const int rc = lbm_get_fields(h, mask, static_cast<uint8_t*>(out) + off * es, out_on_device, out_dtype);
+        if (rc != LBM_OK) {
+            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+            return rc;
+        }
+        off += (size_t)k * h->p.nx * h->p.ny;
+    }
+    return LBM_OK;
+}
+
+size_t lbm_batch_state_bytes(const lbm_batch* b) {
+    if (!b) return 0;
+    size_t n = 0;
+    for (const lbm_handle* h : b->cases) n += lbm_state_bytes(h);
+    return n;
+}
+
+static int batch_state_copy(lbm_batch* b, void* buf, size_t bytes, int32_t on_device, bool get) {
+    if (!b) return LBM_ERR_ARG;
+    if (!buf || bytes < lbm_batch_state_bytes(b)) return b->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_batch_state_bytes()");
+    size_t off = 0;
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+        lbm_handle* h = b->cases[i];
+        const size_t n = lbm_state_bytes(h);
+        uint8_t* p = static_cast<uint8_t*>(buf) + off;
+        const int rc = get ? lbm_get_state(h, p, n, on_device) : lbm_set_state(h, p, n, on_device);
+        if (rc != LBM_OK) {
+            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+            return rc;
+        }
+        off += n;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_state(lbm_batch* b, void* buf, size_t bytes, int32_t on_device) {
+    return batch_state_copy(b, buf, bytes, on_device, true);
+}
+
+int lbm_batch_set_state(lbm_batch* b, const void* buf, size_t bytes, int32_t on_device) {
+    return batch_state_copy(b, const_cast<void*>(buf), bytes, on_device, false);
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_batch_error; }

@@ -10,7 +10,18 @@
 
 #include "lbm.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lbm {
+
+// Host-side NVTX range around a library call (a profiler shows the calls'
+// extents on the timeline; without a tool attached it costs a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Step kernel: a CTA of STRIP_WARPS warps owns STRIP_W consecutive columns and
 // marches up a strip of `strip_h` rows, one thread per column.

@@ -101,6 +101,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_batch_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double), i32,
                                               ctypes.POINTER(i32)]),
         "lbm_batch_set_wait_limit": (ctypes.c_int, [vp, i64, i32]),
+        "lbm_batch_init_macros": (ctypes.c_int, [vp, vp, i32]),
+        "lbm_batch_get_fields": (ctypes.c_int, [vp, ctypes.c_uint32, vp, i32, i32]),
+        "lbm_batch_state_bytes": (sz, [vp]),
+        "lbm_batch_get_state": (ctypes.c_int, [vp, vp, sz, i32]),
+        "lbm_batch_set_state": (ctypes.c_int, [vp, vp, sz, i32]),
         "lbm_batch_destroy": (None, [vp]),
         "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
     }

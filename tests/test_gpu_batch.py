@@ -171,6 +171,64 @@ def test_case_reinitialised_alone_keeps_the_batch_consistent():
     b.close()
 
 
+def test_batch_fields_state_and_restart_match_the_per_case_calls():
+    """lbm_batch_get_fields, lbm_batch_get_state / set_state and
+    lbm_batch_init_macros over uneven shapes: the concatenated buffers hold
+    exactly what the per-case calls give, a restored batch steps to the same
+    bits, and a batch restarted in one call steps to the same bits as one
+    whose cases were restarted one by one."""
+    import torch
+    cases = _cases()
+    names6 = ("phi", "ux", "uy", "p", "c1", "c2")
+    sims = _sims(cases)
+    b = Batch(sims)
+    b.step(7)  # odd: every case's state is in its second buffer
+    cells = sum(w.params["nx"] * w.params["ny"] for w in cases)
+    out = torch.empty(6 * cells, dtype=torch.float64, device="cuda")
+    b.fields(names6, out)
+    got = out.cpu().numpy()
+    off = 0
+    for s in sims:
+        n = s.nx * s.ny
+        f = s.fields(names=names6)
+        for k, name in enumerate(names6):
+            assert np.array_equal(got[off + k * n: off + (k + 1) * n].reshape(s.ny, s.nx), f[name]), name
+        off += 6 * n
+    # checkpoint, step, restore, step again: the same bits
+    buf = b.get_state()
+    assert buf.numel() == b.state_bytes() == sum(s.state_bytes() for s in sims)
+    b.step(5)
+    b.sync()
+    first = [s.fields() for s in sims]
+    b.set_state(buf)
+    b.step(5)
+    b.sync()
+    for k, s in enumerate(sims):
+        again = s.fields()
+        for name in again:
+            assert np.array_equal(again[name], first[k][name]), (k, name)
+    # restart from the concatenated macros in one call, against case by case
+    macros = out.clone()
+    one, each = _sims(cases), _sims(cases)
+    b1, b2 = Batch(one), Batch(each)
+    b1.step(3)
+    b2.step(3)
+    b1.init_macros(macros)
+    off = 0
+    for s in each:
+        n = s.nx * s.ny
+        m = [macros[off + k * n: off + (k + 1) * n].view(s.ny, s.nx) for k in range(6)]
+        s.init_macros(*m)
+        off += 6 * n
+    b1.step(4)
+    b2.step(4)
+    b1.sync()
+    b2.sync()
+    _assert_same(one, each, label="batch restart", tol=0.0)
+    for bb in (b1, b2, b):
+        bb.close()
+
+
 def test_a_withheld_tile_times_out_instead_of_hanging():
     cases = _cases()[:3]
     sims = _sims(cases)
