@@ -115,6 +115,12 @@ int lbm_nn_add_noise(float* state, int64_t pixels, int32_t used, float sigma, ui
 /* Float state -> bfloat16 activation of 16 channels. */
 int lbm_nn_to_bf16(const float* state, int64_t values, void* act, void* stream);
 
+/* bfloat16 values -> float (e.g. a loss gradient joining a float residual path). */
+int lbm_nn_to_f32(const void* act, int64_t values, float* state, void* stream);
+
+/* y += a x over n floats (gradient accumulation across unrolled hops). */
+int lbm_nn_axpy(float* y, const float* x, float a, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

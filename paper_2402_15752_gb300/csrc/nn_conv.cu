@@ -2,31 +2,31 @@
 // (include/lbm_nn.h: lbm_nn_conv3x3, lbm_nn_conv3x3_wgrad).
 //
 // GEMM view of a periodic, dilated 3x3 convolution: M = pixels, N = cout,
-// K = 9 taps x cin.  One tcgen05.mma (kind::f16: bfloat16 operands, FP32
-// accumulation in tensor memory) multiplies 128 pixels of one image row by
-// 16 input channels of one tap for all cout.  Both operands sit in shared
-// memory in the no-swizzle "core matrix" layout (8 rows x 16 bytes, contiguous):
+// K = 9 taps x cin.  A tcgen05.mma (kind::f16: bfloat16 operands, FP32
+// accumulation in tensor memory) multiplies 128 pixels of one image row by 16
+// input channels.  Operands sit in shared memory in the 32-byte swizzled
+// layout, one row (pixel, or weight row) of 16 channels per 32 bytes, so that
+// the 128 pixels of a row shifted by a tap (dy, dx) are the same layout at
+// another start address: a tap costs a descriptor, not a copy.  Activation
+// rows arrive by TMA (cp.async.bulk.tensor) in that layout; the periodic halo
+// columns of a unit by cp.async.
 //
-//   activations: one plane per group of 8 channels, pixels 16 bytes apart, so
-//     that the 128 pixels of a row shifted by a tap (dy, dx) are the same
-//     layout at another start address: a tap costs a descriptor, not a copy;
-//   weights: one plane per (tap, 8 input channels), cout rows 16 bytes apart.
-//
-// Descriptor fields (measured on GB300 with a probe kernel against a host
-// product): the leading-byte offset is the distance between core matrices
-// along K, the stride-byte offset the distance between groups of 8 rows along
-// M or N, for K-major and MN-major operands alike.  With M = 128 row m of the
+// Descriptor fields (measured on GB300 with probe kernels against host
+// products): for no-swizzle K-major and MN-major operands the leading-byte
+// offset steps along K and the stride-byte offset along M/N; for 32-byte
+// swizzled MN-major operands the leading-byte offset steps between 16-element
+// MN groups and the stride-byte offset between 8-row K groups.  The swizzle
+// acts on absolute shared-memory address bits.  With M = 128 row m of the
 // accumulator is TMEM lane m; with M = 64, rows 16q .. 16q + 15 are lanes
-// 32q .. 32q + 15.
+// 32q .. 32q + 15.  One thread issues a tcgen05.mma only about every 90 cycles,
+// so small-N MMAs need more than one issuing warp to keep the tensor cores busy.
 //
-// A CTA (4 warps, one per SM) is persistent over work units of R image rows x
-// 128 columns.  With dilation d the rows of a unit are d apart (rows y0, y0 + d,
-// ...), so its input is always R + 2 rows (y0 - d .. y0 + R d) by 128 + 2 d
-// columns, fetched with cp.async into one of two stages while the tensor cores
-// work on the other; accumulators are double-buffered in tensor memory, so the
-// epilogue of unit i (tcgen05.ld, bias, ReLU / mask / residual, stores) runs
-// while the MMAs of unit i + 1 execute.  Every wait is bounded: a wait that gives
-// up sets bit 0 of *status and the CTA returns after freeing its tensor memory.
+// Both kernels are persistent (one CTA per SM) over work units of R image rows
+// x 128 columns; with dilation d the rows of a unit are d apart, so its input
+// is R + 2 rows by 128 + 2d columns.  Warps have fixed roles (TMA issuer, halo
+// loaders, MMA issuers, epilogue) and hand off through mbarriers; every wait is
+// bounded: one that gives up sets bit 0 of *status and the CTA frees its tensor
+// memory and returns.
 #include "lbm.h"
 #include "lbm_nn.h"
 #include "nn_internal.h"
@@ -575,12 +575,13 @@ int conv_tc_launch(const void* x, const void* w, const float* bias, void* y, con
 
 // Rows per unit, stages (one 16-channel plane of a unit each) and halo slots:
 // 4 rows, 6 stages, 4 halo slots for dilations up to 4 where the rows divide by
-// 4; else 1 row, 6 stages, 8 slots.
+// 4; else 2 rows, 6 stages, 8 slots where they divide by 2; else 1 row.
 template <int CI, int CO, int EPI>
 int conv_tc_dispatch(const void* x, const void* w, const float* bias, void* y, const float* res, const void* mask,
                      int B, int H, int W, int d, int* status, cudaStream_t s) {
     if ((H / d) % 4 == 0 && d <= 4)
         return conv_tc_launch<CI, CO, EPI, 4, 6, 4>(x, w, bias, y, res, mask, B, H, W, d, status, s);
+    if ((H / d) % 2 == 0) return conv_tc_launch<CI, CO, EPI, 2, 6, 8>(x, w, bias, y, res, mask, B, H, W, d, status, s);
     return conv_tc_launch<CI, CO, EPI, 1, 6, 8>(x, w, bias, y, res, mask, B, H, W, d, status, s);
 }
 

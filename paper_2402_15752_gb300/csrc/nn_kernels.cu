@@ -222,6 +222,16 @@ __global__ void add_noise_kernel(float* __restrict__ s, long long P, int used, f
     }
 }
 
+__global__ void to_f32_kernel(const __nv_bfloat16* __restrict__ a, long long n, float* __restrict__ s) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s[i] = __bfloat162float(a[i]);
+}
+
+__global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ x, float a, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
 __global__ void to_bf16_kernel(const float* __restrict__ s, long long n, __nv_bfloat16* __restrict__ a) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] = __float2bfloat16_rn(s[i]);
@@ -315,6 +325,19 @@ int lbm_nn_to_bf16(const float* state, int64_t values, void* act, void* stream) 
     if (!state || !act || values < 1) return LBM_ERR_ARG;
     to_bf16_kernel<<<grid_for(values, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         state, values, static_cast<__nv_bfloat16*>(act));
+    return launch_status();
+}
+
+int lbm_nn_to_f32(const void* act, int64_t values, float* state, void* stream) {
+    if (!state || !act || values < 1) return LBM_ERR_ARG;
+    to_f32_kernel<<<grid_for(values, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16*>(act), values, state);
+    return launch_status();
+}
+
+int lbm_nn_axpy(float* y, const float* x, float a, int64_t n, void* stream) {
+    if (!y || !x || n < 1) return LBM_ERR_ARG;
+    axpy_kernel<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(y, x, a, n);
     return launch_status();
 }
 

@@ -60,7 +60,7 @@ def _status():
 
 # (H, W, dilation): four rows per work unit or one (H / d not a multiple of 4),
 # one or two 128-pixel column blocks, halos that wrap across the image
-SHAPES = [(8, 128, 1), (24, 256, 2), (6, 128, 3), (32, 128, 8)]
+SHAPES = [(8, 128, 1), (24, 256, 2), (6, 128, 3), (32, 128, 8), (5, 128, 1)]
 
 
 @pytest.mark.parametrize("H,W,dil", SHAPES)
@@ -247,24 +247,24 @@ def _bf(a):
     return t.from_numpy(np.asarray(a, dtype=np.float32)).to(t.bfloat16).float().numpy().astype(np.float64)
 
 
-def _grads_with_bf16_storage(x, target, weights, biases):
+def _grads_with_bf16_storage(x, target, weights, biases, dil):
     """The reference's backward pass with the GPU's storage points rounded to
     bfloat16: activations after each ReLU, the loss gradient, and each masked
     input gradient.  Every other operation is the FP64 reference's."""
     acts = [x]
     for l in range(5):
-        acts.append(_bf(np.maximum(cr.conv3x3(acts[-1], weights[l], biases[l]), 0.0)))
-    out = x + cr.conv3x3(acts[5], weights[5], biases[5])
+        acts.append(_bf(np.maximum(cr.conv3x3(acts[-1], weights[l], biases[l], dil[l]), 0.0)))
+    out = x + cr.conv3x3(acts[5], weights[5], biases[5], dil[5])
     npx = out.shape[0] * out.shape[1] * out.shape[2]
     diff = np.zeros_like(out)
     diff[..., :5] = out[..., :5] - target[..., :5]
     dz = _bf(2.0 * diff / (npx * 5))
     gw, gb = [None] * 6, [None] * 6
     for l in range(5, -1, -1):
-        gw[l] = cr.conv3x3_wgrad(acts[l], dz)
+        gw[l] = cr.conv3x3_wgrad(acts[l], dz, dil[l])
         gb[l] = dz.sum(axis=(0, 1, 2))
         if l > 0:
-            dz = _bf(cr.conv3x3_dgrad(dz, weights[l]) * (acts[l] > 0.0))
+            dz = _bf(cr.conv3x3_dgrad(dz, weights[l], dil[l]) * (acts[l] > 0.0))
     return gw, gb
 
 
@@ -299,9 +299,9 @@ def test_network_gradients_match_the_fp64_backward():
     weights = [_host(net.wb[l]) for l in range(6)]
     biases = [_host(net.b32[l]) for l in range(6)]
     xr = x.astype(np.float64)
-    lref, gw, gb = cr.net_loss_and_grads(xr, target, weights, biases)
+    lref, gw, gb = cr.net_loss_and_grads(xr, target, weights, biases, dil=net.dil)
     assert float(loss.item()) == pytest.approx(lref, rel=2e-2)
-    ew_, eb_ = _grads_with_bf16_storage(xr, target.astype(np.float64), weights, biases)
+    ew_, eb_ = _grads_with_bf16_storage(xr, target.astype(np.float64), weights, biases, net.dil)
     for l in range(6):
         gw_gpu, gb_gpu = _host(net.gw[l]), _host(net.gb[l])
         e_store = (np.linalg.norm(gw_gpu - ew_[l]) / np.linalg.norm(ew_[l]),
@@ -311,6 +311,47 @@ def test_network_gradients_match_the_fp64_backward():
         print("\nlayer %d: vs bf16-storage reference %.2e %.2e, vs fp64 %.2e %.2e" % ((l,) + e_store + e_plain))
         assert max(e_store) < 2.5e-2, (l, e_store)
         assert max(e_plain) < 1e-1, (l, e_plain)
+
+
+def test_two_hop_gradients_match_the_fp64_reference():
+    """The unrolled two-hop loss (second hop from the network's own first hop;
+    its input gradient through the residual path and layer 0's adjoint joins
+    the first hop's output gradient) on the GPU against the FP64 reference
+    (oracle/conv_ref.net_two_hop_loss_and_grads), dilated layers.  The GPU keeps
+    the first hop's output, the loss gradients and every activation in
+    bfloat16, so the comparison is norm-wise per layer, as for one hop."""
+    t = _torch()
+    B, H, W = 1, 8, 128
+    dil = (1, 2, 1, 2, 1, 1)
+    net = sg.Net("cuda", seed=7, dilations=dil)
+    ws = sg.Workspace(B, H, W, "cuda", train=True, dilations=dil)
+    two = sg.TwoHop(ws)
+    g = np.random.default_rng(8)
+    x = np.zeros((B, H, W, 16), np.float32)
+    x[..., :5] = g.standard_normal((B, H, W, 5))
+    x = t.from_numpy(x).to(t.bfloat16).float().numpy()
+    t1 = np.zeros_like(x)
+    t1[..., :5] = x[..., :5] + 0.3 * g.standard_normal((B, H, W, 5))
+    t2 = np.zeros_like(x)
+    t2[..., :5] = t1[..., :5] + 0.3 * g.standard_normal((B, H, W, 5))
+    ws.x32.copy_(t.from_numpy(x))
+    ws.x16.copy_(t.from_numpy(x).to(t.bfloat16))
+    ws.t32.copy_(t.from_numpy(t1))
+    two.t2.copy_(t.from_numpy(t2))
+    l1 = t.zeros(1, dtype=t.float64, device="cuda")
+    l2 = t.zeros(1, dtype=t.float64, device="cuda")
+    two.grads(net, l1, l2)
+    _sync()
+    weights = [_host(net.wb[l]) for l in range(6)]
+    biases = [_host(net.b32[l]) for l in range(6)]
+    lref, gw, gb = cr.net_two_hop_loss_and_grads(x.astype(np.float64), t1, t2, weights, biases, dil=dil)
+    assert float(l1.item() + l2.item()) == pytest.approx(lref, rel=2e-2)
+    for l in range(6):
+        ew = np.linalg.norm(_host(net.gw[l]) - gw[l]) / np.linalg.norm(gw[l])
+        eb = np.linalg.norm(_host(net.gb[l]) - gb[l]) / max(np.linalg.norm(gb[l]), 1e-30)
+        print("\ntwo-hop layer %d: weights %.2e, biases %.2e" % (l, ew, eb))
+        assert max(ew, eb) < 1e-1, (l, ew, eb)
+    assert int(net.status.item()) == 0
 
 
 def test_training_reduces_the_loss_and_rollout_judge_falls_back():
@@ -347,26 +388,31 @@ def test_training_reduces_the_loss_and_rollout_judge_falls_back():
 
 
 def test_what_the_network_gains_over_the_solver():
-    """Train on 256 x 256 droplet trajectories of the solver, then time the
-    solver, the network alone and the judged hybrid over 4 hops (64 steps) of 16
-    held-out cases, and state each one's error against the solver.  The network
-    alone is faster per hop; whatever it gets wrong, the judged hybrid must end
-    within the solver's own FP32 agreement of the solver's result whenever it
-    fell back on every judged hop, and finite in any case."""
+    """The shipped network (trained on 2000 buoyant droplet and bubble
+    trajectories of 256 x 256) against the solver on 64 held-out cases of the
+    same family (flow_cases seed 7, 1024 warm-up steps), over 8 hops of 16
+    steps:
+    * the network alone ends nearer the solver's result than the start state
+      does (RMS error below that of predicting no change) in every field;
+    * one network hop is cheaper than the 16 solver steps it replaces;
+    * the judged hybrid (every 4th hop checked on phi and C at the stated
+      tolerance, above the judge's own restart floor) accepts a majority of its
+      judged hops and finishes before the solver alone."""
     import json
     t = _torch()
     dev = t.device("cuda", 0)
-    data = sg.generate(sg.droplet_cases(128, seed=3), snapshots=5, device=dev)
-    shift, scale = sg.normalisation(data)
-    sur = sg.Surrogate(sg.Net(dev, seed=4), shift, scale)
-    sg.train(sur, data, epochs=4, batch=16, lr=1e-3, log=None)
-    del data
-    r = sg.evaluate(sur, sg.droplet_cases(16, seed=11), hops=4, judge_every=2, tol=0.1)
+    sur = sg.Surrogate.load(sg.MODEL_FLOW256, dev)
+    r = sg.evaluate(sur, sg.flow_cases(64, 7), hops=8, judge_every=4, tol=sg.JUDGE_TOL, warm=1024)
     print("\n" + json.dumps(r))
     assert r["network_s"] > 0 and r["solver_s"] > 0 and r["conv_tflops"] > 0
-    # the gain: a network hop is faster than the 16 solver steps it replaces
-    # (measured 1.74x on these 16 cases of 256 x 256, against the batched solver)
-    assert r["speedup_network"] > 1.2, r["speedup_network"]
+    for c in sg.CHANNELS:
+        assert r["error_network_rms"][c] < r["error_no_change_rms"][c], (c, r["error_network_rms"],
+                                                                          r["error_no_change_rms"])
+    # measured 2.8x on these cases against the batched solver
+    assert r["speedup_network"] > 1.5, r["speedup_network"]
+    st = r["judge"]
+    assert st["judged"] == 2 and st["judged"] - st["fallbacks"] > st["judged"] / 2, st
+    # the judge's own floor, measured on the same cases, stays below the tolerance
+    assert r["restart_rms_max_judged"] < sg.JUDGE_TOL, r["restart_rms_max_judged"]
+    assert r["speedup_hybrid"] > 1.0, r["speedup_hybrid"]
     assert all(np.isfinite(v) for v in r["error_hybrid"].values())
-    if r["judge"]["fallbacks"] == r["judge"]["judged"]:
-        assert max(r["error_hybrid"].values()) < 1e-5
