@@ -213,17 +213,9 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
 static int init_common(lbm_handle* h, const double* phi, const double* c1, const double* c2,
                        const double* ux = nullptr, const double* uy = nullptr, const double* p = nullptr) {
     const lbm::InitFields in{phi, ux, uy, p, c1, c2};
-    cudaError_t e = lbm::by_storage(h->p.precision, [&](auto t, auto r) {
-        return lbm::launch_init<decltype(t), decltype(r)>(in, h->pop(0), h->prev(), h->geo, h->cd,
-                                                          h->p.scalar_q, h->stream);
-    });
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
+    const cudaError_t e = h->init_on(in, h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "init kernel", e);
-    h->cur = 0;
-    h->t = 0;
-    h->status_pending = false;
-    h->nonfinite = false;
-    *h->h_status = 0u;
+    h->restarted();
     return LBM_OK;
 }
 
@@ -380,9 +372,7 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device) {
     const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
     if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
     DeviceGuard dg(h->device);
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    cudaError_t e = cudaMemcpyAsync(buf, h->pop(h->cur), a, k, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<uint8_t*>(buf) + a, h->prev(), b, k, h->stream);
+    cudaError_t e = h->copy_state(buf, true, on_device != 0, h->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_state", e);
     return LBM_OK;
@@ -393,17 +383,10 @@ int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_devic
     const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
     if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
     DeviceGuard dg(h->device);
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaError_t e = cudaMemcpyAsync(h->pop(0), buf, a, k, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->prev(), static_cast<const uint8_t*>(buf) + a, b, k, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag(), 0, 16, h->stream);
+    cudaError_t e = h->copy_state(const_cast<void*>(buf), false, on_device != 0, h->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_set_state", e);
-    h->cur = 0;
-    h->t = 0;
-    h->status_pending = false;
-    h->nonfinite = false;
-    *h->h_status = 0u;
+    h->restarted();
     return LBM_OK;
 }
 

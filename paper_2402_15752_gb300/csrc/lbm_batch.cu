@@ -107,7 +107,51 @@ struct lbm_batch {
     lbm::BatchCase* h_cases = nullptr;
     cudaEvent_t cases_ev = nullptr;
     bool cases_ev_live = false;
+    // side streams for the per-case work of the batch-level restart, field and
+    // checkpoint calls: forked from and joined back into `stream` by events
+    static constexpr int NSIDE = 8;
+    cudaStream_t side[NSIDE] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[NSIDE] = {};
+    int nside = 0;
     char err[512] = "";
+
+    cudaError_t make_side_streams() {
+        nside = (int)std::min<size_t>(NSIDE, cases.size());
+        cudaError_t e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+        for (int j = 0; j < nside && e == cudaSuccess; ++j) {
+            e = cudaStreamCreateWithFlags(&side[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev[j], cudaEventDisableTiming);
+        }
+        return e;
+    }
+
+    void free_side_streams() {
+        for (int j = 0; j < NSIDE; ++j) {
+            if (side[j]) cudaStreamDestroy(side[j]);
+            if (join_ev[j]) cudaEventDestroy(join_ev[j]);
+            side[j] = nullptr;
+            join_ev[j] = nullptr;
+        }
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        fork_ev = nullptr;
+    }
+
+    // op(i, s) issues case i's work on stream s; the cases are dealt round-robin
+    // to the side streams, which start after everything queued on `stream` and
+    // which `stream` waits for before anything issued after this call.
+    template <typename Op>
+    cudaError_t fan_out(Op&& op) {
+        cudaError_t e = cudaEventRecord(fork_ev, stream);
+        for (int j = 0; j < nside && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(side[j], fork_ev, 0);
+        if (e != cudaSuccess) return e;
+        for (size_t i = 0; i < cases.size() && e == cudaSuccess; ++i) e = op(i, side[i % nside]);
+        for (int j = 0; j < nside; ++j) {
+            cudaError_t r = cudaEventRecord(join_ev[j], side[j]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(stream, join_ev[j], 0);
+            if (e == cudaSuccess) e = r;
+        }
+        return e;
+    }
 
     lbm::BatchCase* d_cases() const { return reinterpret_cast<lbm::BatchCase*>(ws + L.off_cases); }
     lbm::BatchTile* d_tiles() const { return reinterpret_cast<lbm::BatchTile*>(ws + L.off_tiles); }
@@ -334,6 +378,7 @@ int lbm_batch_create(lbm_handle* const* cases, int32_t ncases, void* d_workspace
     lbm::detail::DeviceGuard dg(b->device);
     cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&b->h_cases), (size_t)ncases * sizeof(lbm::BatchCase));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cases_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = b->make_side_streams();
     rc = e == cudaSuccess ? build_tiling(b, 128, 16) : b->fail(LBM_ERR_CUDA, "lbm_batch_create: staging", e);
     if (rc != LBM_OK) {
         snprintf(g_batch_error, sizeof(g_batch_error), "%s", b->err);
@@ -483,6 +528,7 @@ void lbm_batch_destroy(lbm_batch* b) {
         cudaEventDestroy(b->cases_ev);
     }
     if (b->h_cases) cudaFreeHost(b->h_cases);
+    b->free_side_streams();  // work still queued on them completes first
     delete b;
 }
 
@@ -490,18 +536,36 @@ int lbm_batch_init_macros(lbm_batch* b, const double* macros, int32_t on_device)
     const lbm::NvtxRange range("lbm_batch_init_macros");
     if (!b) return LBM_ERR_ARG;
     if (!macros) return b->fail(LBM_ERR_ARG, "macros is NULL");
-    size_t off = 0;
-    for (size_t i = 0; i < b->cases.size(); ++i) {
+    lbm::detail::DeviceGuard dg(b->device);
+    if (!on_device) {
+        // host fields: each case stages its own copy (pageable memory), in turn
+        size_t off = 0;
+        for (size_t i = 0; i < b->cases.size(); ++i) {
+            lbm_handle* h = b->cases[i];
+            const size_t n = (size_t)h->p.nx * h->p.ny;
+            const double* m = macros + off;
+            const int rc = lbm_init_macros(h, m, m + n, m + 2 * n, m + 3 * n, m + 4 * n, m + 5 * n, 0);
+            if (rc != LBM_OK) {
+                snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+                return rc;
+            }
+            off += 6 * n;
+        }
+        return LBM_OK;
+    }
+    std::vector<size_t> off(b->cases.size());
+    for (size_t i = 0, o = 0; i < b->cases.size(); ++i) {
+        off[i] = o;
+        o += 6 * (size_t)b->cases[i]->p.nx * b->cases[i]->p.ny;
+    }
+    const cudaError_t e = b->fan_out([&](size_t i, cudaStream_t s) {
         lbm_handle* h = b->cases[i];
         const size_t n = (size_t)h->p.nx * h->p.ny;
-        const double* m = macros + off;
-        const int rc = lbm_init_macros(h, m, m + n, m + 2 * n, m + 3 * n, m + 4 * n, m + 5 * n, on_device);
-        if (rc != LBM_OK) {
-            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
-            return rc;
-        }
-        off += 6 * n;
-    }
+        const double* m = macros + off[i];
+        return h->init_on(lbm::InitFields{m, m + n, m + 2 * n, m + 3 * n, m + 4 * n, m + 5 * n}, s);
+    });
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_init_macros", e);
+    for (lbm_handle* h : b->cases) h->restarted();
     return LBM_OK;
 }
 
@@ -511,44 +575,70 @@ int lbm_batch_get_fields(lbm_batch* b, uint32_t mask, void* out, int32_t out_on_
     mask &= LBM_FIELD_ALL;
     if (!mask || !out) return b->fail(LBM_ERR_ARG, "empty field mask or NULL output");
     if (out_dtype != LBM_OUT_F64 && out_dtype != LBM_OUT_F32) return b->fail(LBM_ERR_ARG, "out_dtype must be LBM_OUT_F64 or LBM_OUT_F32");
+    lbm::detail::DeviceGuard dg(b->device);
     const size_t es = out_dtype == LBM_OUT_F64 ? sizeof(double) : sizeof(float);
     int k = 0;
     for (uint32_t m = mask; m; m &= m - 1) ++k;
-    size_t off = 0;
-    for (size_t i = 0; i < b->cases.size(); ++i) {
-        lbm_handle* h = b->cases[i];
-        const int rc = lbm_get_fields(h, mask, static_cast<uint8_t*>(out) + off * es, out_on_device, out_dtype);
-        if (rc != LBM_OK) {
-            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
-            return rc;
-        }
-        off += (size_t)k * h->p.nx * h->p.ny;
+    std::vector<size_t> off(b->cases.size());
+    for (size_t i = 0, o = 0; i < b->cases.size(); ++i) {
+        off[i] = o;
+        o += (size_t)k * b->cases[i]->p.nx * b->cases[i]->p.ny;
     }
+    uint8_t* base = static_cast<uint8_t*>(out);
+    if (!out_on_device) {
+        for (size_t i = 0; i < b->cases.size(); ++i) {
+            lbm_handle* h = b->cases[i];
+            const int rc = lbm_get_fields(h, mask, base + off[i] * es, 0, out_dtype);
+            if (rc != LBM_OK) {
+                snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+                return rc;
+            }
+        }
+        return LBM_OK;
+    }
+    const cudaError_t e = b->fan_out([&](size_t i, cudaStream_t s) {
+        lbm_handle* h = b->cases[i];
+        return h->fields(h->cur, mask, base + off[i] * es, out_dtype == LBM_OUT_F64, s);
+    });
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, "lbm_batch_get_fields", e);
     return LBM_OK;
 }
 
 size_t lbm_batch_state_bytes(const lbm_batch* b) {
     if (!b) return 0;
     size_t n = 0;
-    for (const lbm_handle* h : b->cases) n += lbm_state_bytes(h);
+    for (const lbm_handle* h : b->cases) n += h->state_bytes();
     return n;
 }
 
 static int batch_state_copy(lbm_batch* b, void* buf, size_t bytes, int32_t on_device, bool get) {
     if (!b) return LBM_ERR_ARG;
     if (!buf || bytes < lbm_batch_state_bytes(b)) return b->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_batch_state_bytes()");
-    size_t off = 0;
-    for (size_t i = 0; i < b->cases.size(); ++i) {
-        lbm_handle* h = b->cases[i];
-        const size_t n = lbm_state_bytes(h);
-        uint8_t* p = static_cast<uint8_t*>(buf) + off;
-        const int rc = get ? lbm_get_state(h, p, n, on_device) : lbm_set_state(h, p, n, on_device);
-        if (rc != LBM_OK) {
-            snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
-            return rc;
-        }
-        off += n;
+    lbm::detail::DeviceGuard dg(b->device);
+    std::vector<size_t> off(b->cases.size());
+    for (size_t i = 0, o = 0; i < b->cases.size(); ++i) {
+        off[i] = o;
+        o += b->cases[i]->state_bytes();
     }
+    uint8_t* base = static_cast<uint8_t*>(buf);
+    if (!on_device) {
+        for (size_t i = 0; i < b->cases.size(); ++i) {
+            lbm_handle* h = b->cases[i];
+            const size_t n = h->state_bytes();
+            const int rc = get ? lbm_get_state(h, base + off[i], n, 0) : lbm_set_state(h, base + off[i], n, 0);
+            if (rc != LBM_OK) {
+                snprintf(b->err, sizeof(b->err), "case %zu: %.400s", i, h->err);
+                return rc;
+            }
+        }
+        return LBM_OK;
+    }
+    const cudaError_t e = b->fan_out([&](size_t i, cudaStream_t s) {
+        return b->cases[i]->copy_state(base + off[i], get, true, s);
+    });
+    if (e != cudaSuccess) return b->fail(LBM_ERR_CUDA, get ? "lbm_batch_get_state" : "lbm_batch_set_state", e);
+    if (!get)
+        for (lbm_handle* h : b->cases) h->restarted();
     return LBM_OK;
 }
 

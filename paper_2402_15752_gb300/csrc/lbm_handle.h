@@ -90,6 +90,48 @@ struct lbm_handle {
         });
     }
 
+    // Populations at the equilibria of `in` (buffer 0) and a cleared status
+    // word, on stream s; restarted() then resets the host-side counters.
+    cudaError_t init_on(const lbm::InitFields& in, cudaStream_t s) {
+        cudaError_t e = lbm::by_storage(p.precision, [&](auto t, auto r) {
+            using T = decltype(t);
+            using R = decltype(r);
+            return lbm::launch_init<T, R>(in, pop(0), prev(), geo, coeffs<R>(), p.scalar_q, s);
+        });
+        if (e == cudaSuccess) e = cudaMemsetAsync(flag(), 0, 16, s);
+        return e;
+    }
+
+    void restarted() {
+        cur = 0;
+        t = 0;
+        status_pending = false;
+        nonfinite = false;
+        *h_status = 0u;
+    }
+
+    size_t state_bytes() const { return L.pop_elems * L.elem + L.prev_elems * L.relem; }
+
+    // Checkpoint copies on stream s: the current populations and the previous-step
+    // macros out of (get) or into (set, then buffer 0 and a cleared status word)
+    // the caller's buffer.  After a set the caller calls restarted().
+    cudaError_t copy_state(void* buf, bool get, bool on_device, cudaStream_t s) {
+        const size_t a = L.pop_elems * L.elem, b = L.prev_elems * L.relem;
+        uint8_t* u = static_cast<uint8_t*>(buf);
+        cudaError_t e;
+        if (get) {
+            const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            e = cudaMemcpyAsync(u, pop(cur), a, k, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(u + a, prev(), b, k, s);
+        } else {
+            const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            e = cudaMemcpyAsync(pop(0), u, a, k, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(prev(), u + a, b, k, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(flag(), 0, 16, s);
+        }
+        return e;
+    }
+
     cudaError_t build_graph(int parity) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal);

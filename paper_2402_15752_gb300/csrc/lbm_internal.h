@@ -132,10 +132,10 @@ struct InitFields {
 };
 
 // Initial populations at the equilibria of the given fields, written
-// pre-streamed so the first pulled read returns them.
+// pre-streamed so the first pulled read returns them (arithmetic in R).
 template <typename T, typename R>
 cudaError_t launch_init(const InitFields& in, void* pop, void* prev, const Geometry& geo,
-                        const Coeffs<double>& C, int scalar_q, cudaStream_t s);
+                        const Coeffs<R>& C, int scalar_q, cudaStream_t s);
 
 // phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1t phi, c2 = c2t (1 - phi), into
 // three dense staging arrays (sdf may alias phi).

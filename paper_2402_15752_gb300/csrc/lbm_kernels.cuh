@@ -1086,37 +1086,39 @@ __global__ void __launch_bounds__(STRIP_W, IsHalf<T>::value ? STRIP_MIN_BLOCKS_1
 // With u = 0, p = 0: f_i = w_i phi, g_i = 0, h_k,i = w_i (c_k -/+ S/2).
 template <typename T, typename R, int QS>
 __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ prev, Geometry g,
-                            Coeffs<double> C) {
+                            Coeffs<R> C) {
     constexpr int NQ = nq_of(QS);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= g.nx || y >= g.ny) return;
     const size_t k = (size_t)y * g.nx + x;
-    const double phi = in.phi[k], c1 = in.c1[k], c2 = in.c2[k];
-    const double ux = in.ux ? in.ux[k] : 0.0, uy = in.uy ? in.uy[k] : 0.0, p = in.p ? in.p[k] : 0.0;
-    const double S1 = C.A * mixed_diffusivity(C, phi, 1.0 - phi) * (C.K * c2 * phi - c1 * (1.0 - phi));
-    const double phic = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
-    const double rho = C.rho2 + C.drho * phic, uu = ux * ux + uy * uy;
+    const double phi_d = in.phi[k];
+    const R phi = R(phi_d), c1 = R(in.c1[k]), c2 = R(in.c2[k]);
+    const R ux = in.ux ? R(in.ux[k]) : R(0), uy = in.uy ? R(in.uy[k]) : R(0), p = in.p ? R(in.p[k]) : R(0);
+    const R S1 = C.A * mixed_diffusivity(C, phi, R(1) - phi) * (C.K * c2 * phi - c1 * (R(1) - phi));
+    const R phic = phi < R(0) ? R(0) : (phi > R(1) ? R(1) : phi);
+    const R rho = C.rho2 + C.drho * phic, uu = ux * ux + uy * uy;
     // populations are written pre-streamed: direction i of node (x, y) goes where
     // the next step pulls it from
-    auto put = [&](int plane0, int i, double v) {
+    auto put = [&](int plane0, int i, R v) {
         pop[pop_pull_off<T, NQ>(g, x, y, plane0, i)] = from_r<T>(v);
     };
-    auto cu_of = [&](int i) { return double(cx(i)) * ux + double(cy(i)) * uy; };
+    auto cu_of = [&](int i) { return R(cx(i)) * ux + R(cy(i)) * uy; };
     for (int i = 0; i < 9; ++i) {
-        const double w = w9<double>(i), cu = cu_of(i);
-        const double s = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        double v = (i == 0 ? 3.0 * p * (w - 1.0) : 3.0 * p * w) + rho * s;
+        const R w = w9<R>(i), cu = cu_of(i);
+        const R s = w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        R v = (i == 0 ? R(3) * p * (w - R(1)) : R(3) * p * w) + rho * s;
         put(9, i, g_stored<T>(v));
     }
     if constexpr (PhaseFix<T>::on) {
-        // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31)
+        // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31),
+        // taken from the input in double so that the phase field's total is exact
         int* fp = reinterpret_cast<int*>(pop);
-        const long long Phi = llrint((phi - 0.5) * 2147483648.0);
+        const long long Phi = llrint((phi_d - 0.5) * 2147483648.0);
         long long rest = Phi;
         for (int i = 1; i < 9; ++i) {
-            const double w = w9<double>(i);
-            const long long Fi = llrint((w * phi * (1.0 + 3.0 * cu_of(i)) - 0.5 * w) * 2147483648.0);
+            const R w = w9<R>(i);
+            const long long Fi = llrint(double(w * phi * (R(1) + R(3) * cu_of(i)) - R(0.5) * w) * 2147483648.0);
             rest -= Fi;
             fp[pull_off<NQ>(g, x, y, 0, i)] = (int)Fi;
         }
@@ -1124,40 +1126,40 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
     } else if constexpr (IsHalf<T>::value) {
         // stored as f_i - w_i / 2; the rest population takes what the rounded
         // moving ones leave of phi
-        double sum = 0.0;
+        R sum = R(0);
         for (int i = 1; i < 9; ++i) {
-            const double w = w9<double>(i);
-            const T v = from_r<T>(w * phi * (1.0 + 3.0 * cu_of(i)) - 0.5 * w);
-            sum += double(to_r<float>(v));
+            const R w = w9<R>(i);
+            const T v = from_r<T>(w * phi * (R(1) + R(3) * cu_of(i)) - R(0.5) * w);
+            sum += to_r<R>(v);
             pop[pop_pull_off<T, NQ>(g, x, y, 0, i)] = v;
         }
-        put(0, 0, (phi - 0.5) - sum);
+        put(0, 0, (phi - R(0.5)) - sum);
     } else {
-        for (int i = 0; i < 9; ++i) put(0, i, w9<double>(i) * phi * (1.0 + 3.0 * cu_of(i)));
+        for (int i = 0; i < 9; ++i) put(0, i, w9<R>(i) * phi * (R(1) + R(3) * cu_of(i)));
     }
     R* pp = prev + node_off<5>(g, x, y);
-    pp[0] = R(phi);
-    pp[32] = R(ux);
-    pp[64] = R(uy);
+    pp[0] = phi;
+    pp[32] = ux;
+    pp[64] = uy;
     if (g.one_scalar) {
         // h3 at the equilibrium of Sec. III D for c = c1 + c2; the h2 planes stay 0
-        const double c = c1 + c2, ke = C.K * phic + (1.0 - phic);
+        const R c = c1 + c2, ke = C.K * phic + (R(1) - phic);
         for (int i = 0; i < QS; ++i) {
-            const double w = wq<double, QS>(i);
-            put(18, i, (i == 0 ? c + (w - 1.0) * c / ke : w * c / ke) + 3.0 * w * cu_of(i) * c);
-            put(18 + QS, i, 0.0);
+            const R w = wq<R, QS>(i);
+            put(18, i, (i == 0 ? c + (w - R(1)) * c / ke : w * c / ke) + R(3) * w * cu_of(i) * c);
+            put(18 + QS, i, R(0));
         }
-        pp[96] = R(c);
+        pp[96] = c;
         pp[128] = R(0);
         return;
     }
     for (int i = 0; i < QS; ++i) {
-        const double w = wq<double, QS>(i), e = 1.0 + 3.0 * cu_of(i);
-        put(18, i, w * (c1 * e - 0.5 * S1));
-        put(18 + QS, i, w * (c2 * e + 0.5 * S1));
+        const R w = wq<R, QS>(i), e = R(1) + R(3) * cu_of(i);
+        put(18, i, w * (c1 * e - R(0.5) * S1));
+        put(18 + QS, i, w * (c2 * e + R(0.5) * S1));
     }
-    pp[96] = R(c1);
-    pp[128] = R(c2);
+    pp[96] = c1;
+    pp[128] = c2;
 }
 
 // Block partials of {sum phi, sum(c1 + c2)}; c1 + c2 = sum h1 + sum h2 exactly
@@ -1302,7 +1304,7 @@ cudaError_t launch_variant_impl(const void* src, void* dst, void* prev, const Ge
 
 template <typename T, typename R>
 cudaError_t launch_init_impl(const InitFields& in, void* pop, void* prev, const Geometry& g,
-                             const Coeffs<double>& C, int q, cudaStream_t s) {
+                             const Coeffs<R>& C, int q, cudaStream_t s) {
     dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
     if (q == 5)
         init_kernel<T, R, 5><<<grid, block, 0, s>>>(in, (T*)pop, (R*)prev, g, C);

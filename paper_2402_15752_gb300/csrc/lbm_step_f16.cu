@@ -18,7 +18,7 @@ cudaError_t launch_fields<__half, float>(const void* src, const void* prev, cons
 
 template <>
 cudaError_t launch_init<__half, float>(const InitFields& in, void* pop, void* prev, const Geometry& g,
-                                const Coeffs<double>& C, int q, cudaStream_t s) {
+                                const Coeffs<float>& C, int q, cudaStream_t s) {
     return launch_init_impl<__half, float>(in, pop, prev, g, C, q, s);
 }
 

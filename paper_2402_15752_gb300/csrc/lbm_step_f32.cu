@@ -18,7 +18,7 @@ cudaError_t launch_fields<float, float>(const void* src, const void* prev, const
 
 template <>
 cudaError_t launch_init<float, float>(const InitFields& in, void* pop, void* prev, const Geometry& g,
-                                const Coeffs<double>& C, int q, cudaStream_t s) {
+                                const Coeffs<float>& C, int q, cudaStream_t s) {
     return launch_init_impl<float, float>(in, pop, prev, g, C, q, s);
 }
 
