@@ -55,12 +55,15 @@ extern "C" {
 /* 16-bit population storage, FP32 arithmetic: each population is read, converted
  * and collided in FP32 and rounded stochastically on the store (the random bits
  * are a hash seeded per node and step from the node's coordinates and new macros:
- * deterministic, so runs and restarts are reproducible).  f is stored as the
- * offset f_i - w_i/2 from its value at phi = 1/2, g as it is (bfloat16) or as
- * g_i * 2^10 (half), h as it is; the five previous-step macros stay FP32.  Not in
- * the paper: it halves the population bytes per node (112 -> 56 for scalar_q = 5)
- * at a field error of 1e-3..1e-2 (half); bfloat16 cannot carry the density ratio
- * 1000 bubble.  A step of a 16-bit run also reports a non-finite pressure. */
+ * deterministic, so runs and restarts are reproducible).  Each node also writes
+ * its FP32 pressure and phase field beside its populations, and f and g are
+ * stored as offsets from their writer's: f_i - b_i phi_w and g_i - 3 b_i p_w
+ * (g_0 - 3 (b_0 - 1) p_w), b_i the D2Q9 weights rounded to multiples of 2^-20 so
+ * that they sum to exactly 1; g in half is scaled by 2^10; h is stored as it is;
+ * the five previous-step macros stay FP32.  Not in the paper: 56 population bytes
+ * per node instead of 112 (scalar_q = 5), plus 8 bytes of (p, phi), at a field
+ * error of 1e-4..1e-3 (half) and 1e-3..1e-2 (bfloat16), the density-ratio-1000
+ * bubble included.  A step of a 16-bit run also reports a non-finite pressure. */
 #define LBM_FP32_BF16STORE 2 /* bfloat16 storage (8-bit significand, FP32 range)  */
 #define LBM_FP32_FP16STORE 3 /* IEEE half storage (11-bit significand, |x| < 65504;
                                 values below 6.1e-5 lose bits as subnormals)        */
@@ -185,7 +188,9 @@ int lbm_conserved(lbm_handle* h, double out[2]);
  * produced a NaN/Inf; clears nothing. */
 int lbm_sync(lbm_handle* h);
 
-/* Checkpoint: the populations and previous-step macros of the current state.
+/* Checkpoint: the populations and previous-step macros of the current state,
+ * and with 16-bit storage the (p, phi) FP32 pair of every node that the stored
+ * populations are offsets from (in that order: populations, macros, pairs).
  * lbm_state_bytes gives the size; get/set copy to/from caller memory: a host
  * buffer synchronises the stream, a device buffer (on_device != 0) is copied
  * asynchronously on the handle's stream.  Restoring then stepping is
@@ -219,7 +224,9 @@ int64_t lbm_time(const lbm_handle* h);
  * params: the parameters the state was created with; only the layout fields are read
  * (nx, ny, bc_x, bc_y, scalar_q, precision, scalar_model), the physical ones are
  * ignored, and an invalid layout field returns LBM_ERR_ARG.  d_state: device pointer,
- * 16-byte aligned (LBM_ERR_ARG otherwise), state_bytes >= its population part.  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
+ * 16-byte aligned (LBM_ERR_ARG otherwise), state_bytes >= its population part
+ * (FP64, FP32) or >= lbm_state_bytes (16-bit storage, whose stored phase-field
+ * populations are offsets from the writers' phi in the state's last part).  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
  * host (the call synchronises the stream) or device (out_on_device != 0, asynchronous).
  * err: optional buffer of err_len bytes for an error message (may be NULL). */
 int lbm_conserved_noalloc(const lbm_params* params, const void* d_state, size_t state_bytes,

@@ -65,14 +65,17 @@ Layout layout_of(const lbm_params* p) {
     L.nxb = (p->nx + 31) / 32;
     L.pop_elems = (size_t)p->ny * L.nxb * L.nq * 32;
     L.prev_elems = (size_t)p->ny * L.nxb * 5 * 32;
+    L.pb_elems = L.elem == 2 ? (size_t)p->ny * L.nxb * 32 * 2 : 0;  // (p, phi) of each node
     L.pop_bytes = align_up(L.pop_elems * L.elem, ALIGN);
     L.prev_bytes = align_up(L.prev_elems * L.relem, ALIGN);
+    L.pb_bytes = align_up(L.pb_elems * sizeof(float), ALIGN);
     L.part_bytes = align_up((size_t)lbm::RED_BLOCKS * 2 * sizeof(double), ALIGN);
     L.misc_bytes = ALIGN;
     L.off_pop[0] = 0;
     L.off_pop[1] = L.pop_bytes;
     L.off_prev = 2 * L.pop_bytes;
-    L.off_part = L.off_prev + L.prev_bytes;
+    L.off_pb = L.off_prev + L.prev_bytes;
+    L.off_part = L.off_pb + 2 * L.pb_bytes;
     L.off_misc = L.off_part + L.part_bytes;
     L.total = L.off_misc + L.misc_bytes;
     return L;
@@ -190,6 +193,8 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
     h->geo.strip_h = params->ny;
     h->geo.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
     h->geo.grad_scheme = params->grad_scheme;
+    h->geo.pb_in = nullptr;
+    h->geo.pb_out = nullptr;
     h->cf = coeffs_of<float>(params);
     h->cd = coeffs_of<double>(params);
     h->device = attr.device;
@@ -350,7 +355,7 @@ int lbm_conserved(lbm_handle* h, double out[2]) {
     if (!out) return h->fail(LBM_ERR_ARG, "out is NULL");
     DeviceGuard dg(h->device);
     cudaError_t e = lbm::by_storage(h->p.precision, [&](auto t, auto) {
-        return lbm::launch_conserved<decltype(t)>(h->pop(h->cur), h->geo, h->p.scalar_q, h->partials(), h->sums(),
+        return lbm::launch_conserved<decltype(t)>(h->pop(h->cur), h->geo_from(h->cur), h->p.scalar_q, h->partials(), h->sums(),
                                                   h->stream);
     });
     double tmp[2] = {0.0, 0.0};
@@ -364,13 +369,12 @@ int lbm_conserved(lbm_handle* h, double out[2]) {
 
 size_t lbm_state_bytes(const lbm_handle* h) {
     if (!h) return 0;
-    return h->L.pop_elems * h->L.elem + h->L.prev_elems * h->L.relem;
+    return h->state_bytes();
 }
 
 int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
-    const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
-    if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
+    if (!buf || bytes < h->state_bytes()) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
     DeviceGuard dg(h->device);
     cudaError_t e = h->copy_state(buf, true, on_device != 0, h->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
@@ -380,8 +384,7 @@ int lbm_get_state(lbm_handle* h, void* buf, size_t bytes, int32_t on_device) {
 
 int lbm_set_state(lbm_handle* h, const void* buf, size_t bytes, int32_t on_device) {
     if (!h) return LBM_ERR_ARG;
-    const size_t a = h->L.pop_elems * h->L.elem, b = h->L.prev_elems * h->L.relem;
-    if (!buf || bytes < a + b) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
+    if (!buf || bytes < h->state_bytes()) return h->fail(LBM_ERR_ARG, "state buffer NULL or smaller than lbm_state_bytes()");
     DeviceGuard dg(h->device);
     cudaError_t e = h->copy_state(const_cast<void*>(buf), false, on_device != 0, h->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);

@@ -21,8 +21,9 @@ struct Layout {
     size_t elem, relem; // bytes of a stored population / of a previous-step macro
     int nxb;            // 32-node blocks per row
     size_t pop_elems, prev_elems;
-    size_t pop_bytes, prev_bytes, part_bytes, misc_bytes;
-    size_t off_pop[2], off_prev, off_part, off_misc, total;
+    size_t pb_elems;    // 16-bit storage: floats per pressure-base plane (else 0)
+    size_t pop_bytes, prev_bytes, pb_bytes, part_bytes, misc_bytes;
+    size_t off_pop[2], off_prev, off_pb, off_part, off_misc, total;
 };
 
 // Makes the handle's device current for the duration of a call.
@@ -58,6 +59,15 @@ struct lbm_handle {
 
     void* pop(int k) const { return ws + L.off_pop[k]; }
     void* prev() const { return ws + L.off_prev; }
+    // pressure-base plane that goes with population buffer k (16-bit storage)
+    float* pb(int k) const { return L.pb_elems ? reinterpret_cast<float*>(ws + L.off_pb + k * L.pb_bytes) : nullptr; }
+    // the geometry of a launch that reads population buffer `from`
+    lbm::Geometry geo_from(int from) const {
+        lbm::Geometry g = geo;
+        g.pb_in = pb(from);
+        g.pb_out = pb(from ^ 1);
+        return g;
+    }
     double* partials() const { return reinterpret_cast<double*>(ws + L.off_part); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(ws + L.off_misc); }
     double* sums() const { return reinterpret_cast<double*>(ws + L.off_misc + 16); }
@@ -78,7 +88,8 @@ struct lbm_handle {
         return lbm::by_storage(p.precision, [&](auto t, auto r) {
             using T = decltype(t);
             using R = decltype(r);
-            return lbm::launch_step<T, R>(pop(from), pop(from ^ 1), prev(), geo, coeffs<R>(), p.scalar_q, flag(), s);
+            return lbm::launch_step<T, R>(pop(from), pop(from ^ 1), prev(), geo_from(from), coeffs<R>(), p.scalar_q,
+                                          flag(), s);
         });
     }
 
@@ -86,7 +97,8 @@ struct lbm_handle {
         return lbm::by_storage(p.precision, [&](auto t, auto r) {
             using T = decltype(t);
             using R = decltype(r);
-            return lbm::launch_fields<T, R>(pop(from), prev(), geo, coeffs<R>(), p.scalar_q, mask, out, out_f64, s);
+            return lbm::launch_fields<T, R>(pop(from), prev(), geo_from(from), coeffs<R>(), p.scalar_q, mask, out,
+                                            out_f64, s);
         });
     }
 
@@ -96,7 +108,10 @@ struct lbm_handle {
         cudaError_t e = lbm::by_storage(p.precision, [&](auto t, auto r) {
             using T = decltype(t);
             using R = decltype(r);
-            return lbm::launch_init<T, R>(in, pop(0), prev(), geo, coeffs<R>(), p.scalar_q, s);
+            lbm::Geometry gi = geo;
+            gi.pb_in = nullptr;
+            gi.pb_out = pb(0);  // the first step reads buffer 0
+            return lbm::launch_init<T, R>(in, pop(0), prev(), gi, coeffs<R>(), p.scalar_q, s);
         });
         if (e == cudaSuccess) e = cudaMemsetAsync(flag(), 0, 16, s);
         return e;
@@ -110,23 +125,25 @@ struct lbm_handle {
         *h_status = 0u;
     }
 
-    size_t state_bytes() const { return L.pop_elems * L.elem + L.prev_elems * L.relem; }
+    size_t state_bytes() const { return L.pop_elems * L.elem + L.prev_elems * L.relem + L.pb_elems * sizeof(float); }
 
     // Checkpoint copies on stream s: the current populations and the previous-step
     // macros out of (get) or into (set, then buffer 0 and a cleared status word)
     // the caller's buffer.  After a set the caller calls restarted().
     cudaError_t copy_state(void* buf, bool get, bool on_device, cudaStream_t s) {
-        const size_t a = L.pop_elems * L.elem, b = L.prev_elems * L.relem;
+        const size_t a = L.pop_elems * L.elem, b = L.prev_elems * L.relem, c = L.pb_elems * sizeof(float);
         uint8_t* u = static_cast<uint8_t*>(buf);
         cudaError_t e;
         if (get) {
             const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
             e = cudaMemcpyAsync(u, pop(cur), a, k, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(u + a, prev(), b, k, s);
+            if (e == cudaSuccess && c) e = cudaMemcpyAsync(u + a + b, pb(cur), c, k, s);
         } else {
             const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
             e = cudaMemcpyAsync(pop(0), u, a, k, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(prev(), u + a, b, k, s);
+            if (e == cudaSuccess && c) e = cudaMemcpyAsync(pb(0), u + a + b, c, k, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(flag(), 0, 16, s);
         }
         return e;

@@ -292,6 +292,85 @@ __device__ __forceinline__ R pull_any(const T* __restrict__ src, const Geometry&
     return to_r<R>(ld<CG>(src + node_off<NQ>(g, sx, sy) + (plane0 + i) * 32));
 }
 
+// Node (sx, sy) that population i pulled into (x, y) comes from: the upstream
+// node x - c_i (periodic image), or the node itself behind a wall (half-way
+// bounce-back returns its own population of the opposite direction).
+__device__ __forceinline__ void pull_src(const Geometry& g, int x, int y, int i, int& sx, int& sy) {
+    sx = x - cx(i);
+    sy = y - cy(i);
+    const bool ox = sx < 0 || sx >= g.nx, oy = sy < 0 || sy >= g.ny;
+    if ((ox && g.wall_x) || (oy && g.wall_y)) {
+        sx = x;
+        sy = y;
+        return;
+    }
+    if (ox) sx += sx < 0 ? g.nx : -g.nx;
+    if (oy) sy += sy < 0 ? g.ny : -g.ny;
+}
+
+// 16-bit storage keeps the flow populations as g_i - b_i(p), p the pressure of
+// the node that wrote them: b_i(p) = 3 bw_i p for i > 0 and 3 (bw_0 - 1) p for
+// i = 0, the pressure part of g_i^eq (Eqs. 29-30) up to the base weights bw_i
+// below.  In a light phase the
+// pressure part dominates g_i (p ~ 1e-4 against rho u ~ 1e-6 in the gas of a
+// density-ratio-1000 bubble), so 8 significant bits of g_i carry almost nothing
+// of the momentum; the difference is of the order of rho u and the
+// non-equilibrium part.  The reader adds b_i back with the writer's FP32 p.
+//
+// Base weights b_i of these offsets: the D2Q9 weights rounded to multiples of
+// 2^-20 (116508 / 2^20 = 1/9 - 4e-7, a quarter of that for the diagonals, and
+// the rest weight 466036 / 2^20 = 4/9 + 2e-6), so that they sum to exactly 1
+// and each is exact in FP32.  With the FP32-rounded weights (their sum is
+// 1 + 7.5e-9) every node would gain 7.5e-9 phi per step: the gas of a bubble
+// lost 3.5 nodes of area over 4000 steps on 256 x 512.
+template <typename R>
+__host__ __device__ constexpr R bw9(int i) {
+    return i == 0 ? R(466036.0 / 1048576.0) : (i <= 4 ? R(116508.0 / 1048576.0) : R(29127.0 / 1048576.0));
+}
+template <typename R>
+__device__ __forceinline__ R p_base(int i, R p) {
+    return i == 0 ? (R(3) * (bw9<R>(0) - R(1))) * p : (R(3) * bw9<R>(i)) * p;
+}
+// ... and the phase-field populations as f_i - bw_i phi_w, phi_w the phase field
+// of the node that wrote them (the equilibrium of Eq. 24 at rest, up to the
+// base weights).  Stored
+// whole (or as f_i - w_i / 2), their 8-bit rounding put noise of ~1e-3 into phi
+// in the bulk phases, and the surface-tension force of that noise, divided by
+// the gas density, drove the gas velocity; the remainder is of the order of
+// w_i phi c_i.u and the non-equilibrium part.  One fused multiply-add decodes
+// it, the same one wherever a population is read.
+__device__ __forceinline__ float f_dec(float stored, int i, float phw) { return fmaf(bw9<float>(i), phw, stored); }
+
+// Pressure and phase field of the writers (16-bit storage): one float pair
+// (p, phi) per node at pair index y * nxb * 32 + x of Geometry::pb_in / pb_out.
+// The column of a thread, for the pair index of the node population i pulled
+// into (x, y) comes from (pull_src) without the general wrap and wall tests in
+// rows 1 .. ny - 2.
+struct PbCol {
+    int x, xm, xp;  // the column and its periodic x neighbours
+    bool bl, br;    // behind a left / right x wall
+};
+__device__ __forceinline__ PbCol pb_col(const Geometry& g, int x) {
+    PbCol c;
+    c.x = x;
+    c.xm = x == 0 ? g.nx - 1 : x - 1;
+    c.xp = x == g.nx - 1 ? 0 : x + 1;
+    c.bl = g.wall_x && x == 0;
+    c.br = g.wall_x && x == g.nx - 1;
+    return c;
+}
+__device__ __forceinline__ long long pb_src(const Geometry& g, const PbCol& c, int y, int i, bool inner) {
+    int sx, sy;
+    if (inner) {
+        const bool bb = (cx(i) == 1 && c.bl) || (cx(i) == -1 && c.br);
+        sx = bb ? c.x : (cx(i) == 1 ? c.xm : (cx(i) == -1 ? c.xp : c.x));
+        sy = bb ? y : y - cy(i);
+    } else {
+        pull_src(g, c.x, y, i, sx, sy);
+    }
+    return (long long)sy * (g.nxb * 32) + sx;
+}
+
 // omp = 1 - phi, passed separately so that it keeps full precision near phi = 1
 // FP32 uses the hardware-approximation intrinsics (a few ulp; the parity budget
 // is 1e-5), FP64 the IEEE operations.
@@ -351,8 +430,8 @@ template <typename T>
 struct PhaseFix { static constexpr bool on = false; using S = T; };
 template <>
 struct PhaseFix<float> { static constexpr bool on = true; using S = int; };
-// 16-bit storage: f is stored as f_i - w_i / 2 (offset from the weights at
-// phi = 1/2) and handled in FP32 once loaded
+// 16-bit storage: f is stored as f_i - bw_i phi_w (f_dec) and handled in FP32
+// once loaded
 template <>
 struct PhaseFix<__half> { static constexpr bool on = false; using S = float; };
 template <>
@@ -362,7 +441,7 @@ struct PhaseFix<__nv_bfloat16> { static constexpr bool on = false; using S = flo
 template <typename T, bool CG = false>
 __device__ __forceinline__ typename PhaseFix<T>::S load_f(const T* __restrict__ src, long long off, int i) {
     if constexpr (PhaseFix<T>::on) return ld<CG>(reinterpret_cast<const int*>(src) + off);
-    else if constexpr (IsHalf<T>::value) return to_r<float>(ld<CG>(src + off)) + 0.5f * w9<float>(i);
+    else if constexpr (IsHalf<T>::value) return to_r<float>(ld<CG>(src + off));  // f_i - bw_i phi_w (see f_dec)
     else return ld<CG>(src + off);
 }
 constexpr float FIX_ONE = 2147483648.0f;                 // 2^31
@@ -407,9 +486,9 @@ struct NodeFH {
 // halves ride along with f and are used one row later
 template <typename T, typename R, int QS>
 struct NodeFH<T, R, QS, true> {
-    uint32_t fg[9];   // (f_i - w_i / 2, g_i stored form)
+    uint32_t fg[9];   // (f_i - bw_i phi_w, g_i - b_i(p_w)): see f_dec, p_base
     uint32_t hh[QS];  // (h1_i, h2_i)
-    __device__ __forceinline__ float F(int i) const { return lo16<T>(fg[i]) + 0.5f * w9<float>(i); }
+    __device__ __forceinline__ float F(int i) const { return lo16<T>(fg[i]); }
     __device__ __forceinline__ float G(int i) const { return hi16<T>(fg[i]); }
     __device__ __forceinline__ float H1(int i) const { return lo16<T>(hh[i]); }
     __device__ __forceinline__ float H2(int i) const { return hi16<T>(hh[i]); }
@@ -537,6 +616,27 @@ __device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS
     else solve_scalars(C, phi, omp, P1, P2, c1, c2);
 }
 
+// The same for 16-bit storage, the stored f decoded with the phase fields phs
+// of the nodes they were pulled from (f_dec), summed in phase_sum's order.
+template <typename T, typename R, int QS, bool ONE = false>
+__device__ __forceinline__ void zeroth_b(const Coeffs<R>& C, const NodeFH<T, R, QS>& P, const float (&phs)[9],
+                                         float& phis, R& phi, R& c1, R& c2) {
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = f_dec(P.F(i), i, phs[i]);
+    phis = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
+    phi = R(phis);
+    const R omp = R(1) - R(phis);
+    R P1 = R(0), P2 = R(0);
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+        P1 += P.H1(i);
+        P2 += P.H2(i);
+    }
+    if constexpr (ONE) henry_split(C, phi, P1, c1, c2);
+    else solve_scalars(C, phi, omp, P1, P2, c1, c2);
+}
+
 // D2Q9 stencils of phi at the ring centre column X (Eqs. 41-42).  Fixed-point
 // phi: the differences and the Laplacian's sums are exact integers, converted
 // once; the cubic of Eq. (4) gets the low bits of phi through its derivative.
@@ -617,21 +717,26 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
         stcs(o, phi - sum);
     }
 }
-// The same for 16-bit storage: the stored forms f*_i - w_i / 2, rounded
-// stochastically, go to fs (they are written together with g*_i); the rest
-// population takes what the rounded moving ones leave of phi.
+// The same for 16-bit storage: the pulled f decoded with their writers' phase
+// fields phs; the stored forms f*_i - bw_i phi (phi: this node's, written beside
+// them), rounded stochastically, go to fs (written together with g*_i).  With
+// f*_i - bw_i phi = (1 - w_f)(f_i - bw_i phi) + w_f (w_i - bw_i) phi + w_i c_i.B,
+// and the rest population taking what the moving ones leave of phi, its stored
+// form is minus the sum of the rounded moving ones (the bw_i sum to 1).
 template <typename T, typename R, int QS>
-__device__ __forceinline__ void collide_f16(T (&fs)[9], const NodeFH<T, R, QS>& P, R phi, R omega, R Bx,
-                                            R By, uint32_t key) {
-    const R a0 = omega * phi, keep = R(1) - omega;
+__device__ __forceinline__ void collide_f16(T (&fs)[9], const NodeFH<T, R, QS>& P, const float (&phs)[9], R phi,
+                                            R omega, R Bx, R By, uint32_t key) {
+    const R keep = R(1) - omega;
     R sum = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-        fs[i] = store_value<T>(keep * P.F(i) + w9<R>(i) * (a0 + cB) - R(0.5) * w9<R>(i), key, i);
-        sum += to_r<R>(fs[i]) + R(0.5) * w9<R>(i);
+        const R d = R(f_dec(P.F(i), i, phs[i])) - bw9<R>(i) * phi;
+        const R dw = R(w9<double>(i) - bw9<double>(i));  // folded: i is unrolled
+        fs[i] = store_value<T>(keep * d + w9<R>(i) * cB + (dw * omega) * phi, key, i);
+        sum += to_r<R>(fs[i]);
     }
-    fs[0] = store_value<T>(phi - sum - R(0.5) * w9<R>(0), key, 0);
+    fs[0] = store_value<T>(-sum, key, 0);
 }
 
 // One tile of the fused step (FIELDS = false) or of the macroscopic-field
@@ -698,6 +803,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     };
     int doff[9];
     column_offsets(rx, doff);
+    const int pb_row = g.nxb * 32;  // pairs per row of the writers' (p, phi) plane
     __shared__ int s_hoff[2][9];  // the halo nodes' offsets
     if (halo) {
         int hd[9];
@@ -737,6 +843,22 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         }
     }
 
+    // 16-bit storage: the phase fields of the writers of the pulled f.  Off the
+    // x boundary columns and the first and last rows the writers are the 3 x 3
+    // neighbourhood: three row pointers and constant offsets.
+    auto writer_phases = [&](const PbCol& pc, int ry, bool y_in, float (&phs)[9]) {
+        if (y_in && pc.x >= 1 && pc.x <= g.nx - 2) {
+            const float* c = g.pb_in + 2 * ((long long)ry * pb_row + pc.x) + 1;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) phs[i] = ld<CG>(c + 2 * (-cy(i) * pb_row - cx(i)));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) phs[i] = ld<CG>(g.pb_in + 2 * pb_src(g, pc, ry, i, y_in) + 1);
+        }
+    };
+    const PbCol pcol = pb_col(g, rx);
+    const PbCol hcolp = pb_col(g, hx);
+
     // zeroth moments of row yy into ring slot yy & 3; the pulled pops go to P
     auto moments_row = [&](int yy, NodeFH<T, R, QS>& P) {
         const int ry = resolve(yy, g.ny, g.wall_y);
@@ -744,6 +866,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         PS phis;
         R phi, c1, c2;
         uint32_t hv = 0;
+        float phs[9];
         if (y_in) {
             pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, rx, ry), doff, P);
             if constexpr (HALO_SPLIT) {
@@ -752,7 +875,12 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         } else {
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
         }
-        zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
+        if constexpr (PAIRED) {
+            writer_phases(pcol, ry, y_in, phs);
+            zeroth_b<T, R, QS, ONE>(C, P, phs, phis, phi, c1, c2);
+        } else {
+            zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
+        }
         if constexpr (CUR_SMEM) P.save(&s_cur[yy & 1][tid], W);
         s_phi[yy & 3][tid + 1] = phis;
         s_c[yy & 3][0][tid + 1] = c1;
@@ -783,7 +911,12 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, hx, ry), s_hoff[tid == 0 ? 0 : 1], hp);
             else
                 pull_fh_any<QS, T, R, CG, ONE>(src, g, hx, ry, hp);
-            zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
+            if constexpr (PAIRED) {
+                writer_phases(hcolp, ry, y_in, phs);
+                zeroth_b<T, R, QS, ONE>(C, hp, phs, hs, a, b, c);
+            } else {
+                zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
+            }
             s_phi[yy & 3][hcol] = hs;
             s_c[yy & 3][0][hcol] = b;
             s_c[yy & 3][1][hcol] = c;
@@ -799,11 +932,27 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         const long long nd = node_off<NQL>(g, x, y);
         // ---- a. loads of row y: g (pulled) and the previous-step macros ----
         R gp[9], pv[5];
+        float phw[9];  // 16-bit storage: phase fields of the writers of the pulled f
         if (col_in) {
             if constexpr (PAIRED) {
-                // pulled with f one row ago
+                // pulled with f one row ago; stored relative to the writer's
+                // pressure part (p_base), which is added back here with the
+                // writer's p; its phi decodes f in the collision
+                float2 wr[9];
+                const float2* pb2 = reinterpret_cast<const float2*>(g.pb_in);
+                if (inner && x >= 1 && x <= g.nx - 2) {
+                    const float2* c = pb2 + (long long)y * pb_row + x;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid])));
+                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(c + (-cy(i) * pb_row - cx(i)));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(pb2 + pb_src(g, pcol, y, i, inner));
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid]))) + p_base<R>(i, R(wr[i].x));
+                    phw[i] = wr[i].y;
+                }
             } else if (inner) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ld<CG>(src + nd + doff[i] + (9 + i) * 32)));
@@ -949,7 +1098,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     const R sharp = C.force_f * C.four_over_W * phi * omp;
                     const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
                     const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
-                    if constexpr (PAIRED) collide_f16<T, R, QS>(fs, cur, phi, C.omega_f, Bx, By, key);
+                    if constexpr (PAIRED) collide_f16<T, R, QS>(fs, cur, phw, phi, C.omega_f, Bx, By, key);
                     else collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By, key);
                 }
                 // ---- e2. g (Eqs. 28-31) ----
@@ -967,11 +1116,14 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
                         R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
                         if (i == 0) v -= R(3) * omega_g * p;
+                        if constexpr (PAIRED) v -= p_base<R>(i, p);
                         const T gv = store_value<T>(g_stored<T>(v), key, 9 + i);
                         if constexpr (PAIRED) stcs(ow + i * 32, pack16<T>(fs[i], gv));
                         else stcs(o + (9 + i) * 32, gv);
                     }
                 }
+                if constexpr (PAIRED)
+                    reinterpret_cast<float2*>(g.pb_out)[(long long)y * pb_row + x] = make_float2(float(p), float(phi));
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
                 if constexpr (ONE) {
                     // ---- e3'. h3: one-scalar model (Sec. III D) ----
@@ -1108,8 +1260,16 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
         const R w = w9<R>(i), cu = cu_of(i);
         const R s = w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         R v = (i == 0 ? R(3) * p * (w - R(1)) : R(3) * p * w) + rho * s;
+        if constexpr (IsHalf<T>::value) {
+            // relative to the pressure part of the node this slot is pulled from
+            int sx, sy;
+            pull_src(g, x, y, i, sx, sy);
+            v -= p_base<R>(i, in.p ? R(in.p[(size_t)sy * g.nx + sx]) : R(0));
+        }
         put(9, i, g_stored<T>(v));
     }
+    if constexpr (IsHalf<T>::value)
+        reinterpret_cast<float2*>(g.pb_out)[(size_t)y * g.nxb * 32 + x] = make_float2(float(p), float(phi));
     if constexpr (PhaseFix<T>::on) {
         // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31),
         // taken from the input in double so that the phase field's total is exact
@@ -1124,16 +1284,20 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
         }
         fp[pull_off<NQ>(g, x, y, 0, 0)] = (int)rest;
     } else if constexpr (IsHalf<T>::value) {
-        // stored as f_i - w_i / 2; the rest population takes what the rounded
-        // moving ones leave of phi
+        // stored as f_i - w_i phi_w, phi_w the phase field of the node the slot
+        // is pulled from (f_dec); the rest population, pulled from the node
+        // itself, takes what the rounded moving ones leave of phi
         R sum = R(0);
         for (int i = 1; i < 9; ++i) {
             const R w = w9<R>(i);
-            const T v = from_r<T>(w * phi * (R(1) + R(3) * cu_of(i)) - R(0.5) * w);
-            sum += to_r<R>(v);
+            int sx, sy;
+            pull_src(g, x, y, i, sx, sy);
+            const R phs = R(float(in.phi[(size_t)sy * g.nx + sx]));
+            const T v = from_r<T>(w * phi * (R(1) + R(3) * cu_of(i)) - bw9<R>(i) * phs);
+            sum += to_r<R>(v) + bw9<R>(i) * phs;
             pop[pop_pull_off<T, NQ>(g, x, y, 0, i)] = v;
         }
-        put(0, 0, (phi - R(0.5)) - sum);
+        put(0, 0, (phi - sum) - bw9<R>(0) * phi);
     } else {
         for (int i = 0; i < 9; ++i) put(0, i, w9<R>(i) * phi * (R(1) + R(3) * cu_of(i)));
     }
@@ -1181,6 +1345,9 @@ __global__ void __launch_bounds__(RED_THREADS)
             ai += s;
         } else {
             for (int i = 0; i < 9; ++i) a += double(load_f<T>(pop, pop_pull_off<T, NQ>(g, x, y, 0, i), i));
+            // 16-bit storage: every node's phi_w is the base of the nine slots its
+            // populations went to, with weights summing to 1
+            if constexpr (IsHalf<T>::value) a += double(g.pb_in[2 * ((long long)y * g.nxb * 32 + x) + 1]);
         }
         double c = 0.0;
         for (int i = 0; i < QS; ++i)

@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(NA_THREADS)
             ai += s;
         } else {
             for (int i = 0; i < 9; ++i) a += double(lbm::load_f<T>(pop, lbm::pop_pull_off<T, NQ>(g, x, y, 0, i), i));
+            // 16-bit storage: plus the writers' phase fields (the base of the stored f)
+            if constexpr (lbm::IsHalf<T>::value) a += double(g.pb_in[2 * ((long long)y * g.nxb * 32 + x) + 1]);
         }
         for (int i = 0; i < QS; ++i)
             b += lbm::pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
@@ -156,6 +158,12 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     const size_t elem = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
     const size_t pop_bytes = (size_t)params->ny * nxb * lbm::nq_of(qs) * 32 * elem;
     if (state_bytes < pop_bytes) return na_fail(err, err_len, LBM_ERR_ARG, "state smaller than the populations of these parameters");
+    // 16-bit storage: the writers' (p, phi) pairs follow the populations and the
+    // previous-step macros (lbm_get_state's layout); phi is part of the stored f
+    const size_t pb_off = pop_bytes + (size_t)params->ny * nxb * 5 * 32 * sizeof(float);
+    const size_t pb_bytes = elem == 2 ? (size_t)params->ny * nxb * 32 * 2 * sizeof(float) : 0;
+    if (elem == 2 && state_bytes < pb_off + pb_bytes)
+        return na_fail(err, err_len, LBM_ERR_ARG, "16-bit state smaller than lbm_state_bytes() of these parameters");
 
     int dev = 0;
     cudaPointerAttributes attr;
@@ -196,6 +204,8 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     g.strip_h = params->ny;
     g.one_scalar = params->scalar_model == LBM_SCALAR_ONE;
     g.grad_scheme = params->grad_scheme;
+    g.pb_in = elem == 2 ? reinterpret_cast<const float*>(static_cast<const uint8_t*>(d_state) + pb_off) : nullptr;
+    g.pb_out = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = lbm::by_storage(params->precision, [&](auto t, auto) {
         return na_launch<decltype(t)>(d_state, g, qs, scratch, (int)nchunks, s);
