@@ -935,24 +935,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         float phw[9];  // 16-bit storage: phase fields of the writers of the pulled f
         if (col_in) {
             if constexpr (PAIRED) {
-                // pulled with f one row ago; stored relative to the writer's
-                // pressure part (p_base), which is added back here with the
-                // writer's p; its phi decodes f in the collision
-                float2 wr[9];
-                const float2* pb2 = reinterpret_cast<const float2*>(g.pb_in);
-                if (inner && x >= 1 && x <= g.nx - 2) {
-                    const float2* c = pb2 + (long long)y * pb_row + x;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(c + (-cy(i) * pb_row - cx(i)));
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(pb2 + pb_src(g, pcol, y, i, inner));
-                }
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid]))) + p_base<R>(i, R(wr[i].x));
-                    phw[i] = wr[i].y;
-                }
+                // decoded after the row barrier below: held from here through the
+                // look-ahead row they pushed the kernel into spilling
             } else if (inner) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gp[i] = g_value<T>(to_r<R>(ld<CG>(src + nd + doff[i] + (9 + i) * 32)));
@@ -973,6 +957,27 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         if constexpr (CUR_SMEM) cur.load(&s_cur[y & 1][tid], W);
 
         if (col_in) {
+            if constexpr (PAIRED) {
+                // g pulled with f one row ago (this thread's words of the shared
+                // slot, which the look-ahead row does not touch), stored relative
+                // to the writer's pressure part (p_base), added back here with the
+                // writer's p; the writer's phi decodes f in the collision
+                float2 wr[9];
+                const float2* pb2 = reinterpret_cast<const float2*>(g.pb_in);
+                if (inner && x >= 1 && x <= g.nx - 2) {
+                    const float2* c = pb2 + (long long)y * pb_row + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(c + (-cy(i) * pb_row - cx(i)));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(pb2 + pb_src(g, pcol, y, i, inner));
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid]))) + p_base<R>(i, R(wr[i].x));
+                    phw[i] = wr[i].y;
+                }
+            }
             // ---- c. stencils (Eqs. 41-42, D2Q9 weights) from the shared ring ----
             const int X = tid + 1;
             const PhiStencil<T, R> st = phi_stencil<T, R, W2>(s_phi[(y - 1) & 3], s_phi[y & 3],
