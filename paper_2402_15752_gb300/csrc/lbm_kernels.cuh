@@ -137,12 +137,6 @@ __device__ __forceinline__ float hi16(uint32_t w) {
     if constexpr (std::is_same<T, __half>::value) return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
     else return __uint_as_float(w & 0xffff0000u);
 }
-__device__ __forceinline__ unsigned short bits16(__half v) { return __half_as_ushort(v); }
-__device__ __forceinline__ unsigned short bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
-template <typename T>
-__device__ __forceinline__ uint32_t pack16(T lo, T hi) {
-    return (uint32_t)bits16(lo) | ((uint32_t)bits16(hi) << 16);
-}
 
 // IEEE half storage keeps g_i * 2^10: the flow populations are of the order of
 // the pressure (1e-6 .. 1e-2 in lattice units), much of which lies below half's
@@ -170,12 +164,18 @@ __device__ __forceinline__ R g_stored(R v) {
 // slow diffusive and sharpening updates of the populations -- are not rounded
 // away every step as they are under round-to-nearest.
 //
+// The two populations of a stored word are rounded and packed by one hardware
+// conversion with stochastic rounding (cvt.rs.{bf16x2,f16x2}.f32, Blackwell):
+// for bfloat16 it adds the random bits r & 0xffff (low value) and r >> 16 (high
+// value) to the float encodings and truncates; for half, bits 0-12 and 16-28 of
+// r round the 13 dropped significand bits (subnormals at their own spacing).
+//
 // Random bits: a seed per node and step (the 32-bit finalizer of MurmurHash3
 // applied to the node's coordinates and the bits of its new macros) is xored
-// with the bits of the value to round and multiplied by an odd constant per
-// population (a multiplicative hash, Knuth's Fibonacci hashing); the top bits
-// are used.  For a uniform seed the product is uniform whatever the value, so
-// the rounding stays unbiased, and a run is deterministic: graph and plain
+// with the bits of the word's low value and multiplied by an odd constant per
+// word (a multiplicative hash, Knuth's Fibonacci hashing).  For a uniform seed
+// the product's low and high halves are uniform and independent of the value,
+// so the rounding stays unbiased, and a run is deterministic: graph and plain
 // launches, and a restart from a checkpoint, give the same bits.
 __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h ^= h >> 16;
@@ -185,39 +185,26 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
-// random word for population q (0 .. 35) of a node with seed h, value bits vb
-__device__ __forceinline__ uint32_t sr_bits(uint32_t h, uint32_t vb, int q) {
-    return (h ^ vb) * (0x9e3779b9u + (uint32_t)q * 0x3c6ef372u);
+// random word for stored word j (0 .. 17) of a node with seed h, low value lo
+__device__ __forceinline__ uint32_t sr_word(uint32_t h, float lo, int j) {
+    return (h ^ __float_as_uint(lo)) * (0x9e3779b9u + (uint32_t)j * 0x3c6ef372u);
 }
-// v rounded to T with the random word r: a uniform fraction of one ulp of the
-// 16-bit grid at |v| is added to |v| and the sum truncated.
+// lo and hi rounded stochastically to T with the random word r, packed as one
+// stored word (lo in the low half); lo16 / hi16 read the rounded values back
 template <typename T>
-__device__ __forceinline__ T round16_stochastic(float v, uint32_t r) {
-    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        // bfloat16 is the upper half of the float's encoding: add 16 random bits
-        // to the low half and truncate (a carry moves into the exponent, where
-        // the grid spacing doubles as the encoding's does)
-        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
-    } else {
-        // half: one ulp at |v| is 2^(e - 10), e = max(exponent of |v|, -14) (the
-        // spacing stays 2^-24 below 2^-14, so the sum is formed in float
-        // arithmetic); the fraction is the top 24 bits of r
-        const float a = fabsf(v);
-        const float m = fmaxf(a, 0x1p-14f);
-        const float ulp24 = __uint_as_float((__float_as_uint(m) & 0x7f800000u) - (34u << 23));  // 2^(e-34)
-        return __float2half_rz(copysignf(fmaf(float(r >> 8), ulp24, a), v));
-    }
+__device__ __forceinline__ uint32_t round_pair(float lo, float hi, uint32_t r) {
+    uint32_t w;
+    if constexpr (std::is_same<T, __half>::value)
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(hi), "f"(lo), "r"(r));
+    else
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(w) : "f"(hi), "f"(lo), "r"(r));
+    return w;
 }
-// A value of the arithmetic type R as stored in T: 16-bit storage rounds
-// stochastically (node seed h, population q), FP32/FP64 storage converts exactly.
+// A value of the arithmetic type R as stored in T (FP32 / FP64 storage: exact).
 template <typename T, typename R>
-__device__ __forceinline__ T store_value(R v, uint32_t h, int q) {
-    if constexpr (IsHalf<T>::value) {
-        const float f = float(v);
-        return round16_stochastic<T>(f, sr_bits(h, __float_as_uint(f), q));
-    } else {
-        return T(v);
-    }
+__device__ __forceinline__ T store_value(R v) {
+    static_assert(!IsHalf<T>::value, "16-bit storage rounds word pairs (round_pair)");
+    return T(v);
 }
 
 // Node coordinate seen by a stencil: periodic wrap, or the mirror ghost of
@@ -684,8 +671,7 @@ __device__ __forceinline__ PhiStencil<T, R> phi_stencil(const typename PhaseFix<
 // phi - sum_{i>0} f*_i, so sum f* = phi exactly.
 template <typename T, typename R>
 __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename PhaseFix<T>::S (&f)[9],
-                                          typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By,
-                                          uint32_t key) {
+                                          typename PhaseFix<T>::S phis, R phi, R omega, R Bx, R By) {
     if constexpr (PhaseFix<T>::on) {
         // f*_i - f_i = w_f (w_i phi - f_i) + w_i c_i . B.  In the offset encoding
         // w_i phi - f_i = w_i Phi - F_i (the w_i / 2 offsets cancel); Phi - 9 F_i
@@ -718,25 +704,23 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
     }
 }
 // The same for 16-bit storage: the pulled f decoded with their writers' phase
-// fields phs; the stored forms f*_i - bw_i phi (phi: this node's, written beside
-// them), rounded stochastically, go to fs (written together with g*_i).  With
+// fields phs; the forms to store, f*_i - bw_i phi (phi: this node's, written
+// beside them), go to fv[1..8] unrounded: each is rounded stochastically together
+// with g*_i, the other half of its word.  With
 // f*_i - bw_i phi = (1 - w_f)(f_i - bw_i phi) + w_f (w_i - bw_i) phi + w_i c_i.B,
 // and the rest population taking what the moving ones leave of phi, its stored
 // form is minus the sum of the rounded moving ones (the bw_i sum to 1).
 template <typename T, typename R, int QS>
-__device__ __forceinline__ void collide_f16(T (&fs)[9], const NodeFH<T, R, QS>& P, const float (&phs)[9], R phi,
-                                            R omega, R Bx, R By, uint32_t key) {
+__device__ __forceinline__ void collide_f16(float (&fv)[9], const NodeFH<T, R, QS>& P, const float (&phs)[9], R phi,
+                                            R omega, R Bx, R By) {
     const R keep = R(1) - omega;
-    R sum = R(0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
         const R d = R(f_dec(P.F(i), i, phs[i])) - bw9<R>(i) * phi;
         const R dw = R(w9<double>(i) - bw9<double>(i));  // folded: i is unrolled
-        fs[i] = store_value<T>(keep * d + w9<R>(i) * cB + (dw * omega) * phi, key, i);
-        sum += to_r<R>(fs[i]);
+        fv[i] = float(keep * d + w9<R>(i) * cB + (dw * omega) * phi);
     }
-    fs[0] = store_value<T>(-sum, key, 0);
 }
 
 // One tile of the fused step (FIELDS = false) or of the macroscopic-field
@@ -1098,13 +1082,13 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                                      : 0u;
 
                 // ---- e1. f (Eqs. 23-25) ----
-                T fs[9];  // 16-bit storage: f*, stored with g*
+                float fv[9];  // 16-bit storage: f* to store, rounded with g*
                 {
                     const R sharp = C.force_f * C.four_over_W * phi * omp;
                     const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
                     const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
-                    if constexpr (PAIRED) collide_f16<T, R, QS>(fs, cur, phw, phi, C.omega_f, Bx, By, key);
-                    else collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By, key);
+                    if constexpr (PAIRED) collide_f16<T, R, QS>(fv, cur, phw, phi, C.omega_f, Bx, By);
+                    else collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By);
                 }
                 // ---- e2. g (Eqs. 28-31) ----
                 {
@@ -1114,17 +1098,26 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     const R gam = R(4.5) * omega_g * rho;
                     const R del = R(3) * force_g * C.drho;
                     const R keep = R(1) - omega_g;
+                    float fsum = 0.0f;  // 16-bit storage: the rounded stored f*_1..8
+                    // moving populations first: with 16-bit storage the rest f* is
+                    // minus the sum of the rounded moving ones
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
+                    for (int k = 0; k < 9; ++k) {
+                        const int i = PAIRED ? (k + 1) % 9 : k;
                         const R cu = (cx(i) ? R(cx(i)) * ux : R(0)) + (cy(i) ? R(cy(i)) * uy : R(0));
                         const R cg = (cx(i) ? R(cx(i)) * dphix : R(0)) + (cy(i) ? R(cy(i)) * dphiy : R(0));
                         const R cV = (cx(i) ? R(cx(i)) * Vx : R(0)) + (cy(i) ? R(cy(i)) * Vy : R(0));
                         R v = keep * gp[i] + w9_times(i, alpha + cV + cu * (gam * cu + del * cg));
                         if (i == 0) v -= R(3) * omega_g * p;
-                        if constexpr (PAIRED) v -= p_base<R>(i, p);
-                        const T gv = store_value<T>(g_stored<T>(v), key, 9 + i);
-                        if constexpr (PAIRED) stcs(ow + i * 32, pack16<T>(fs[i], gv));
-                        else stcs(o + (9 + i) * 32, gv);
+                        if constexpr (PAIRED) {
+                            v -= p_base<R>(i, p);
+                            const float fo = i == 0 ? -fsum : fv[i];
+                            const uint32_t wv = round_pair<T>(fo, float(g_stored<T>(v)), sr_word(key, fo, i));
+                            if (i != 0) fsum += lo16<T>(wv);
+                            stcs(ow + i * 32, wv);
+                        } else {
+                            stcs(o + (9 + i) * 32, store_value<T>(v));
+                        }
                     }
                 }
                 if constexpr (PAIRED)
@@ -1150,11 +1143,11 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     for (int i = 1; i < QS; ++i) {
                         const R w = wq<R, QS>(i);
                         const R cB = (cx(i) ? R(cx(i)) * B3x : R(0)) + (cy(i) ? R(cy(i)) * B3y : R(0));
-                        const T v = store_value<T>(k3 * cur.H1(i) + w * (a3 + cB), key, 18 + i);
+                        const T v = store_value<T>(k3 * cur.H1(i) + w * (a3 + cB));
                         s1 += to_r<R>(v);
                         stcs(o + (18 + i) * 32, v);
                     }
-                    stcs(o + 18 * 32, store_value<T>(P1 - s1, key, 18));
+                    stcs(o + 18 * 32, store_value<T>(P1 - s1));
                 } else {
                     if constexpr (GS >= 1) {
                         // local grad c1, grad c2 (Eq. 39) from the first moments of h1, h2
@@ -1194,27 +1187,30 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         const R w = wq<R, QS>(i);
                         const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
                         const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
-                        const T v1 = store_value<T>(k1 * cur.H1(i) + w * (a1 + c1B), key, 18 + i);
-                        const T v2 = store_value<T>(k2 * cur.H2(i) + w * (a2 + c2B), key, 18 + QS + i);
-                        s1 += to_r<R>(v1);
-                        s2 += to_r<R>(v2);
+                        const R v1 = k1 * cur.H1(i) + w * (a1 + c1B);
+                        const R v2 = k2 * cur.H2(i) + w * (a2 + c2B);
                         if constexpr (PAIRED) {
-                            stcs(ow + (9 + i) * 32, pack16<T>(v1, v2));
+                            const uint32_t wv = round_pair<T>(float(v1), float(v2), sr_word(key, float(v1), 9 + i));
+                            s1 += lo16<T>(wv);
+                            s2 += hi16<T>(wv);
+                            stcs(ow + (9 + i) * 32, wv);
                         } else {
-                            stcs(o + (18 + i) * 32, v1);
-                            stcs(o + (18 + QS + i) * 32, v2);
+                            const T t1 = store_value<T>(v1), t2 = store_value<T>(v2);
+                            s1 += to_r<R>(t1);
+                            s2 += to_r<R>(t2);
+                            stcs(o + (18 + i) * 32, t1);
+                            stcs(o + (18 + QS + i) * 32, t2);
                         }
                     }
                     // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
                     // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
                     // without c1 they cannot inherit its rounding, and P1 + P2 is kept
-                    const T r1 = store_value<T>((P1 + (S1 - Ht)) - s1, key, 18);
-                    const T r2 = store_value<T>((P2 - (S1 - Ht)) - s2, key, 18 + QS);
+                    const R r1 = (P1 + (S1 - Ht)) - s1, r2 = (P2 - (S1 - Ht)) - s2;
                     if constexpr (PAIRED) {
-                        stcs(ow + 9 * 32, pack16<T>(r1, r2));
+                        stcs(ow + 9 * 32, round_pair<T>(float(r1), float(r2), sr_word(key, float(r1), 9)));
                     } else {
-                        stcs(o + 18 * 32, r1);
-                        stcs(o + (18 + QS) * 32, r2);
+                        stcs(o + 18 * 32, store_value<T>(r1));
+                        stcs(o + (18 + QS) * 32, store_value<T>(r2));
                     }
                 }
             }
