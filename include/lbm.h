@@ -168,7 +168,10 @@ int lbm_init_macros(lbm_handle* h, const double* phi, const double* ux, const do
                     const double* p, const double* c1, const double* c2, int32_t on_device);
 
 /* Advance nsteps >= 0 time steps (asynchronous).  Returns LBM_ERR_NONFINITE if an
- * earlier call's steps, already finished on the GPU, produced a NaN/Inf. */
+ * earlier call's steps, already finished on the GPU, produced a NaN/Inf.  Steps
+ * are replayed from captured CUDA graphs of 32, 16, .., 2 steps (the binary
+ * digits of nsteps), an odd last step is one plain launch; the first call with
+ * nsteps >= 2 captures them (call it before any stream capture of your own). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of the current state (the zeroth/first moments of the current

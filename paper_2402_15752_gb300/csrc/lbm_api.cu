@@ -282,11 +282,21 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     DeviceGuard dg(h->device);
     int64_t left = nsteps;
     cudaError_t e = cudaSuccess;
-    if (left >= lbm::detail::GRAPH_STEPS) {
-        if (!h->graph[h->cur]) e = h->build_graph(h->cur);
+    // n = 32 a + the binary digits of the rest: captured sequences of 32, 16,
+    // .., 2 steps (even: the state stays in buffer cur), then at most one
+    // plain launch
+    if (left >= 2) {
+        using lbm::detail::GRAPH_LEVELS;
+        e = h->build_graphs();
         while (e == cudaSuccess && left >= lbm::detail::GRAPH_STEPS) {
-            e = cudaGraphLaunch(h->graph[h->cur], h->stream);
-            left -= lbm::detail::GRAPH_STEPS;  // even count: the state stays in buffer cur
+            e = cudaGraphLaunch(h->graph[h->cur][GRAPH_LEVELS - 1], h->stream);
+            left -= lbm::detail::GRAPH_STEPS;
+        }
+        for (int lv = GRAPH_LEVELS - 2; lv >= 0 && e == cudaSuccess; --lv) {
+            if (left >= (2 << lv)) {
+                e = cudaGraphLaunch(h->graph[h->cur][lv], h->stream);
+                left -= 2 << lv;
+            }
         }
     }
     while (e == cudaSuccess && left > 0) {
@@ -400,7 +410,8 @@ void lbm_destroy(lbm_handle* h) {
     {
         DeviceGuard dg(h->device);
         if (h->stream || h->capture) cudaStreamSynchronize(h->stream);
-        for (auto& g : h->graph) if (g) cudaGraphExecDestroy(g);
+        for (auto& row : h->graph)
+            for (auto& g : row) if (g) cudaGraphExecDestroy(g);
         if (h->status_ev) cudaEventDestroy(h->status_ev);
         if (h->capture) cudaStreamDestroy(h->capture);
         if (h->h_status) cudaFreeHost(h->h_status);

@@ -14,7 +14,10 @@
 namespace lbm {
 namespace detail {
 
-constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity is kept)
+// Captured step sequences: level k replays 2^(k+1) steps (2, 4, .., 32), one
+// graph per starting buffer.  Even lengths keep the state in its buffer.
+constexpr int GRAPH_LEVELS = 5;
+constexpr int GRAPH_STEPS = 2 << (GRAPH_LEVELS - 1);  // the longest: 32 steps
 
 struct Layout {
     int nq;             // populations per node
@@ -50,7 +53,7 @@ struct lbm_handle {
     uint8_t* ws = nullptr;
     int cur = 0;
     int64_t t = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2][lbm::detail::GRAPH_LEVELS] = {};  // [starting buffer][level]
     unsigned* h_status = nullptr;
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
@@ -149,18 +152,27 @@ struct lbm_handle {
         return e;
     }
 
-    cudaError_t build_graph(int parity) {
+    cudaError_t build_graph(int parity, int level) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         int c = parity;
         cudaError_t le = cudaSuccess;
-        for (int k = 0; k < lbm::detail::GRAPH_STEPS && le == cudaSuccess; ++k, c ^= 1) le = step_once(c, capture);
+        for (int k = 0; k < (2 << level) && le == cudaSuccess; ++k, c ^= 1) le = step_once(c, capture);
         e = cudaStreamEndCapture(capture, &g);
         if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
         if (e != cudaSuccess) return e;
-        e = cudaGraphInstantiate(&graph[parity], g, 0);
+        e = cudaGraphInstantiate(&graph[parity][level], g, 0);
         cudaGraphDestroy(g);
+        return e;
+    }
+    // Every level for both starting buffers, on the first call that steps at
+    // least twice, so that later calls of any length launch no capture.
+    cudaError_t build_graphs() {
+        cudaError_t e = cudaSuccess;
+        for (int parity = 0; parity < 2; ++parity)
+            for (int level = 0; level < lbm::detail::GRAPH_LEVELS && e == cudaSuccess; ++level)
+                if (!graph[parity][level]) e = build_graph(parity, level);
         return e;
     }
 

@@ -285,7 +285,7 @@ def test_checkpoint_and_graph_are_bit_identical(storage):
     w = wl.droplet64(nx=50, ny=41, R=11.0, rho2=0.3, mu2=0.04)
     init = ("sdf", w.sdf, 1.0, 0.2)
     a = run_gpu(w.params, init, 0, storage)
-    a.step(40)  # one graph of 32 steps plus 8 single launches
+    a.step(40)  # graphs of 32 and 8 steps
     b = run_gpu(w.params, init, 0, storage, chunks=[1] * 40)
     fa, fb = a.fields(), b.fields()
     for k in fa:
