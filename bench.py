@@ -311,9 +311,10 @@ def run_ours(args, rank, world, local):
     relem = 8 if args.precision == "fp64" else 4          # bytes of a previous-step macro
     bytes_per_cell = 2 * (18 + 2 * q) * elem + 2 * 5 * relem
     if elem == 2:
-        # 16-bit storage: the writer's (p, phi) pair (FP32), written beside its
-        # populations and read once for the populations pulled from it
-        bytes_per_cell += 2 * 8
+        # 16-bit storage: the writer's bases, (p, phi) in FP32 and (c1, c2) in
+        # halves, written beside its populations and read once for the
+        # populations pulled from it
+        bytes_per_cell += 2 * 12
     launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_cell * cells / launch_s / 1e9
     peak, peak_kind = hbm_peak()

@@ -54,14 +54,16 @@ extern "C" {
 #define LBM_FP32           1 /* FP32 storage and arithmetic                      */
 /* 16-bit population storage, FP32 arithmetic: each population is read, converted
  * and collided in FP32 and rounded stochastically on the store (the random bits
- * are a hash seeded per node and step from the node's coordinates and new macros:
- * deterministic, so runs and restarts are reproducible).  Each node also writes
- * its FP32 pressure and phase field beside its populations, and f and g are
- * stored as offsets from their writer's: f_i - b_i phi_w and g_i - 3 b_i p_w
- * (g_0 - 3 (b_0 - 1) p_w), b_i the D2Q9 weights rounded to multiples of 2^-20 so
- * that they sum to exactly 1; g in half is scaled by 2^10; h is stored as it is;
- * the five previous-step macros stay FP32.  Not in the paper: 56 population bytes
- * per node instead of 112 (scalar_q = 5), plus 8 bytes of (p, phi), at a field
+ * are a hash seeded per node and step from the node's coordinates, its new macros
+ * and a step counter kept in the state: deterministic, so runs and restarts are
+ * reproducible).  Each node also writes
+ * its pressure and phase field (FP32) and its scalars (rounded to IEEE half)
+ * beside its populations, which are stored as offsets from their writer's: f_i - b_i phi_w,
+ * g_i - 3 b_i p_w (g_0 - 3 (b_0 - 1) p_w) and h_k,i - bq_i c_k,w, b_i and bq_i the
+ * D2Q9 and scalar-lattice weights rounded to multiples of 2^-20 so that they sum
+ * to exactly 1; g in half is scaled by 2^10; the five previous-step macros stay
+ * FP32.  Not in the paper: 56 population bytes per node instead of 112
+ * (scalar_q = 5), plus 12 bytes of (p, phi, c1, c2), at a field
  * error of 1e-4..1e-3 (half) and 1e-3..1e-2 (bfloat16), the density-ratio-1000
  * bubble included.  A step of a 16-bit run also reports a non-finite pressure. */
 #define LBM_FP32_BF16STORE 2 /* bfloat16 storage (8-bit significand, FP32 range)  */
@@ -136,8 +138,9 @@ typedef struct lbm_handle lbm_handle;
 
 /* Bytes of device workspace the parameters need (0 if the parameters are invalid).
  * Layout per node: two population buffers (28 values for scalar_q = 5, 36 for 9, of
- * 8, 4 or 2 bytes), five previous-step macros (8 bytes for LBM_FP64, else 4), plus a
- * few KB of reduction partials and flags. */
+ * 8, 4 or 2 bytes), five previous-step macros (8 bytes for LBM_FP64, else 4), with
+ * 16-bit storage two sets of the writers' (p, phi, c1, c2) bases (12 bytes per node each),
+ * plus a few KB of reduction partials and flags. */
 size_t lbm_workspace_bytes(const lbm_params* params);
 
 /* Validate parameters (Sec. III relaxation-time relations: every tau > 1/2),
@@ -192,8 +195,9 @@ int lbm_conserved(lbm_handle* h, double out[2]);
 int lbm_sync(lbm_handle* h);
 
 /* Checkpoint: the populations and previous-step macros of the current state,
- * and with 16-bit storage the (p, phi) FP32 pair of every node that the stored
- * populations are offsets from (in that order: populations, macros, pairs).
+ * and with 16-bit storage the (p, phi) FP32 and (c1, c2) half bases of every node that the stored
+ * populations are offsets from and the step counter of the rounding (in that order:
+ * populations, macros, bases, counter).
  * lbm_state_bytes gives the size; get/set copy to/from caller memory: a host
  * buffer synchronises the stream, a device buffer (on_device != 0) is copied
  * asynchronously on the handle's stream.  Restoring then stepping is
@@ -228,8 +232,8 @@ int64_t lbm_time(const lbm_handle* h);
  * (nx, ny, bc_x, bc_y, scalar_q, precision, scalar_model), the physical ones are
  * ignored, and an invalid layout field returns LBM_ERR_ARG.  d_state: device pointer,
  * 16-byte aligned (LBM_ERR_ARG otherwise), state_bytes >= its population part
- * (FP64, FP32) or >= lbm_state_bytes (16-bit storage, whose stored phase-field
- * populations are offsets from the writers' phi in the state's last part).  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
+ * (FP64, FP32) or >= lbm_state_bytes (16-bit storage, whose stored f and h are
+ * offsets from the writers' phi, c1 and c2 in the state's last part).  cuda_stream: stream to run on (NULL = legacy default).  out: 2 doubles,
  * host (the call synchronises the stream) or device (out_on_device != 0, asynchronous).
  * err: optional buffer of err_len bytes for an error message (may be NULL). */
 int lbm_conserved_noalloc(const lbm_params* params, const void* d_state, size_t state_bytes,

@@ -65,7 +65,9 @@ Layout layout_of(const lbm_params* p) {
     L.nxb = (p->nx + 31) / 32;
     L.pop_elems = (size_t)p->ny * L.nxb * L.nq * 32;
     L.prev_elems = (size_t)p->ny * L.nxb * 5 * 32;
-    L.pb_elems = L.elem == 2 ? (size_t)p->ny * L.nxb * 32 * 2 : 0;  // (p, phi) of each node
+    // per node (p, phi) in FP32 and (c1, c2) in halves, then the step counter
+    // (and a pad word)
+    L.pb_elems = L.elem == 2 ? (size_t)p->ny * L.nxb * 32 * 3 + 2 : 0;
     L.pop_bytes = align_up(L.pop_elems * L.elem, ALIGN);
     L.prev_bytes = align_up(L.prev_elems * L.relem, ALIGN);
     L.pb_bytes = align_up(L.pb_elems * sizeof(float), ALIGN);

@@ -24,7 +24,7 @@ struct Layout {
     size_t elem, relem; // bytes of a stored population / of a previous-step macro
     int nxb;            // 32-node blocks per row
     size_t pop_elems, prev_elems;
-    size_t pb_elems;    // 16-bit storage: floats per pressure-base plane (else 0)
+    size_t pb_elems;    // 16-bit storage: 4-byte words per plane of the writers' bases (else 0)
     size_t pop_bytes, prev_bytes, pb_bytes, part_bytes, misc_bytes;
     size_t off_pop[2], off_prev, off_pb, off_part, off_misc, total;
 };
@@ -62,7 +62,7 @@ struct lbm_handle {
 
     void* pop(int k) const { return ws + L.off_pop[k]; }
     void* prev() const { return ws + L.off_prev; }
-    // pressure-base plane that goes with population buffer k (16-bit storage)
+    // plane of the writers' bases that goes with population buffer k (16-bit storage)
     float* pb(int k) const { return L.pb_elems ? reinterpret_cast<float*>(ws + L.off_pb + k * L.pb_bytes) : nullptr; }
     // the geometry of a launch that reads population buffer `from`
     lbm::Geometry geo_from(int from) const {

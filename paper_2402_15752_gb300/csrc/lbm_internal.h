@@ -63,11 +63,11 @@ struct Geometry {
     int strip_h;     // rows per CTA of the step kernel
     int one_scalar;  // one-scalar model: h1 planes hold h3, h2 planes unused
     int grad_scheme; // 0: stencils (Eq. 41); 1: local grad c (Eq. 39); 2: also local grad phi
-    // 16-bit storage only (else NULL): the pressure of the node that wrote each
-    // stored flow population, one float per node at y * nxb * 32 + x, read for
-    // the populations a launch pulls (pb_in) and written beside the ones it
-    // stores (pb_out).  Set per launch: the two planes alternate with the
-    // population buffers.
+    // 16-bit storage only (else NULL): the bases of the node that wrote each
+    // stored population, (p, phi) in FP32 then (c1, c2) in halves, per node
+    // at y * nxb * 32 + x, read for the populations a launch pulls (pb_in) and
+    // written beside the ones it stores (pb_out).  Set per launch: the two
+    // planes alternate with the population buffers.
     const float* pb_in;
     float* pb_out;
 };

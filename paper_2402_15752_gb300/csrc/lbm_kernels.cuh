@@ -314,6 +314,13 @@ template <typename R>
 __host__ __device__ constexpr R bw9(int i) {
     return i == 0 ? R(466036.0 / 1048576.0) : (i <= 4 ? R(116508.0 / 1048576.0) : R(29127.0 / 1048576.0));
 }
+// ... and of the scalar populations, stored as h_k,i - bq_i c_k,w with c_k,w the
+// writer's FP32 c_k: the D2Q5 weights rounded the same way (174763 / 2^20 =
+// 1/6 + 3e-7 on the axes, the rest 349524 / 2^20), the D2Q9 ones for scalar_q = 9.
+template <typename R, int QS>
+__host__ __device__ constexpr R bwq(int i) {
+    return QS == 5 ? (i == 0 ? R(349524.0 / 1048576.0) : R(174763.0 / 1048576.0)) : bw9<R>(i);
+}
 template <typename R>
 __device__ __forceinline__ R p_base(int i, R p) {
     return i == 0 ? (R(3) * (bw9<R>(0) - R(1))) * p : (R(3) * bw9<R>(i)) * p;
@@ -328,9 +335,24 @@ __device__ __forceinline__ R p_base(int i, R p) {
 // it, the same one wherever a population is read.
 __device__ __forceinline__ float f_dec(float stored, int i, float phw) { return fmaf(bw9<float>(i), phw, stored); }
 
-// Pressure and phase field of the writers (16-bit storage): one float pair
-// (p, phi) per node at pair index y * nxb * 32 + x of Geometry::pb_in / pb_out.
-// The column of a thread, for the pair index of the node population i pulled
+// Writers' bases (16-bit storage), per node at index k = y * nxb * 32 + x:
+// the FP32 pair (p, phi) at floats 2k, 2k + 1 of Geometry::pb_in / pb_out, and
+// (c1, c2) as two IEEE halves in word k of the plane that follows (from float
+// 2 N on, N = ny * nxb * 32); then the step counter (word 3 N).  The writer
+// stores its populations as offsets from these values and the reader adds the
+// same values back: rounding c1, c2 to half only leaves a slightly larger
+// remainder of h to store (half's 11 bits keep it far below the remainder of
+// the equilibrium).  phi and p stay FP32: the decoded f are summed into phi
+// every step, and the FP32 rounding of b_i phi_w + stored, with phi_w on the
+// coarse half grid, repeats the same way every step of a steady state and
+// drifts the phase field.
+__device__ __forceinline__ float half_lo(uint32_t w) { return lo16<__half>(w); }
+__device__ __forceinline__ float half_hi(uint32_t w) { return hi16<__half>(w); }
+__device__ __forceinline__ uint32_t half_pair(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+// The column of a thread, for the index of the node that population i pulled
 // into (x, y) comes from (pull_src) without the general wrap and wall tests in
 // rows 1 .. ny - 2.
 struct PbCol {
@@ -604,10 +626,11 @@ __device__ __forceinline__ void zeroth(const Coeffs<R>& C, const NodeFH<T, R, QS
 }
 
 // The same for 16-bit storage, the stored f decoded with the phase fields phs
-// of the nodes they were pulled from (f_dec), summed in phase_sum's order.
+// of the nodes they were pulled from (f_dec), summed in phase_sum's order; the
+// stored h decoded by adding cb1 = sum_i bq_i c1_w,i and cb2 (the writers' c).
 template <typename T, typename R, int QS, bool ONE = false>
 __device__ __forceinline__ void zeroth_b(const Coeffs<R>& C, const NodeFH<T, R, QS>& P, const float (&phs)[9],
-                                         float& phis, R& phi, R& c1, R& c2) {
+                                         float cb1, float cb2, float& phis, R& phi, R& c1, R& c2) {
     float f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = f_dec(P.F(i), i, phs[i]);
@@ -620,6 +643,8 @@ __device__ __forceinline__ void zeroth_b(const Coeffs<R>& C, const NodeFH<T, R, 
         P1 += P.H1(i);
         P2 += P.H2(i);
     }
+    P1 += R(cb1);
+    P2 += R(cb2);
     if constexpr (ONE) henry_split(C, phi, P1, c1, c2);
     else solve_scalars(C, phi, omp, P1, P2, c1, c2);
 }
@@ -703,21 +728,20 @@ __device__ __forceinline__ void collide_f(T* __restrict__ o, const typename Phas
         stcs(o, phi - sum);
     }
 }
-// The same for 16-bit storage: the pulled f decoded with their writers' phase
-// fields phs; the forms to store, f*_i - bw_i phi (phi: this node's, written
-// beside them), go to fv[1..8] unrounded: each is rounded stochastically together
-// with g*_i, the other half of its word.  With
+// The same for 16-bit storage: fd are the pulled f decoded with their writers'
+// phase fields (f_dec); the forms to store, f*_i - bw_i phi (phi: this node's,
+// written beside them), go to fv[1..8] unrounded: each is rounded
+// stochastically together with g*_i, the other half of its word.  With
 // f*_i - bw_i phi = (1 - w_f)(f_i - bw_i phi) + w_f (w_i - bw_i) phi + w_i c_i.B,
 // and the rest population taking what the moving ones leave of phi, its stored
 // form is minus the sum of the rounded moving ones (the bw_i sum to 1).
-template <typename T, typename R, int QS>
-__device__ __forceinline__ void collide_f16(float (&fv)[9], const NodeFH<T, R, QS>& P, const float (&phs)[9], R phi,
-                                            R omega, R Bx, R By) {
+template <typename R>
+__device__ __forceinline__ void collide_f16(float (&fv)[9], const float (&fd)[9], R phi, R omega, R Bx, R By) {
     const R keep = R(1) - omega;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const R cB = (cx(i) ? R(cx(i)) * Bx : R(0)) + (cy(i) ? R(cy(i)) * By : R(0));
-        const R d = R(f_dec(P.F(i), i, phs[i])) - bw9<R>(i) * phi;
+        const R d = R(fd[i]) - bw9<R>(i) * phi;
         const R dw = R(w9<double>(i) - bw9<double>(i));  // folded: i is unrolled
         fv[i] = float(keep * d + w9<R>(i) * cB + (dw * omega) * phi);
     }
@@ -787,7 +811,20 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     };
     int doff[9];
     column_offsets(rx, doff);
-    const int pb_row = g.nxb * 32;  // pairs per row of the writers' (p, phi) plane
+    const int pb_row = g.nxb * 32;  // nodes per row of the writers' bases planes
+    // 16-bit storage: the (c1, c2) half pairs of the writers' bases
+    const uint32_t* pb_c = PAIRED ? reinterpret_cast<const uint32_t*>(g.pb_in + 2LL * g.ny * pb_row) : nullptr;
+    // 16-bit storage: the step counter kept after the last node of the bases
+    // plane (read from the input plane, written incremented to the output one
+    // by the first CTA of a step launch); it seeds the stochastic rounding, so
+    // that a value that stays the same from step to step is not rounded the
+    // same way every step
+    uint32_t tstep = 0;
+    if constexpr (PAIRED) {
+        const long long cnt = 3LL * g.ny * pb_row;  // in 4-byte words
+        tstep = ld<CG>(reinterpret_cast<const uint32_t*>(g.pb_in) + cnt);
+        if (!FIELDS && x0 == 0 && ya == 0 && tid == 0) reinterpret_cast<uint32_t*>(g.pb_out)[cnt] = tstep + 1u;
+    }
     __shared__ int s_hoff[2][9];  // the halo nodes' offsets
     if (halo) {
         int hd[9];
@@ -827,17 +864,28 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         }
     }
 
-    // 16-bit storage: the phase fields of the writers of the pulled f.  Off the
-    // x boundary columns and the first and last rows the writers are the 3 x 3
-    // neighbourhood: three row pointers and constant offsets.
-    auto writer_phases = [&](const PbCol& pc, int ry, bool y_in, float (&phs)[9]) {
+    // 16-bit storage: the writers' bases of the pulled populations: phase fields
+    // phs of the writers of f, and sum_i bq_i c_k,w,i of the writers of h.  Off
+    // the x boundary columns and the first and last rows the writers are the
+    // 3 x 3 neighbourhood: one row pointer and constant offsets.
+    auto writer_bases = [&](const PbCol& pc, int ry, bool y_in, float (&phs)[9], float& cb1, float& cb2) {
+        cb1 = 0.0f;
+        cb2 = 0.0f;
+        auto take = [&](int i, long long k) {
+            phs[i] = ld<CG>(g.pb_in + 2 * k + 1);
+            if (i < QS) {
+                const uint32_t cw = ld<CG>(pb_c + k);
+                cb1 = fmaf(bwq<float, QS>(i), half_lo(cw), cb1);
+                cb2 = fmaf(bwq<float, QS>(i), half_hi(cw), cb2);
+            }
+        };
         if (y_in && pc.x >= 1 && pc.x <= g.nx - 2) {
-            const float* c = g.pb_in + 2 * ((long long)ry * pb_row + pc.x) + 1;
+            const long long c = (long long)ry * pb_row + pc.x;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) phs[i] = ld<CG>(c + 2 * (-cy(i) * pb_row - cx(i)));
+            for (int i = 0; i < 9; ++i) take(i, c + (-cy(i) * pb_row - cx(i)));
         } else {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) phs[i] = ld<CG>(g.pb_in + 2 * pb_src(g, pc, ry, i, y_in) + 1);
+            for (int i = 0; i < 9; ++i) take(i, pb_src(g, pc, ry, i, y_in));
         }
     };
     const PbCol pcol = pb_col(g, rx);
@@ -850,7 +898,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         PS phis;
         R phi, c1, c2;
         uint32_t hv = 0;
-        float phs[9];
+        float phs[9], cb1, cb2;
         if (y_in) {
             pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, rx, ry), doff, P);
             if constexpr (HALO_SPLIT) {
@@ -860,8 +908,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
         }
         if constexpr (PAIRED) {
-            writer_phases(pcol, ry, y_in, phs);
-            zeroth_b<T, R, QS, ONE>(C, P, phs, phis, phi, c1, c2);
+            writer_bases(pcol, ry, y_in, phs, cb1, cb2);
+            zeroth_b<T, R, QS, ONE>(C, P, phs, cb1, cb2, phis, phi, c1, c2);
         } else {
             zeroth<T, R, QS, ONE>(C, P, phis, phi, c1, c2);
         }
@@ -896,8 +944,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             else
                 pull_fh_any<QS, T, R, CG, ONE>(src, g, hx, ry, hp);
             if constexpr (PAIRED) {
-                writer_phases(hcolp, ry, y_in, phs);
-                zeroth_b<T, R, QS, ONE>(C, hp, phs, hs, a, b, c);
+                writer_bases(hcolp, ry, y_in, phs, cb1, cb2);
+                zeroth_b<T, R, QS, ONE>(C, hp, phs, cb1, cb2, hs, a, b, c);
             } else {
                 zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
             }
@@ -916,7 +964,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         const long long nd = node_off<NQL>(g, x, y);
         // ---- a. loads of row y: g (pulled) and the previous-step macros ----
         R gp[9], pv[5];
-        float phw[9];  // 16-bit storage: phase fields of the writers of the pulled f
+        // 16-bit storage: the pulled f and h, decoded with their writers' bases
+        float fd[PAIRED ? 9 : 1], h1d[PAIRED ? QS : 1], h2d[PAIRED ? QS : 1];
         if (col_in) {
             if constexpr (PAIRED) {
                 // decoded after the row barrier below: held from here through the
@@ -946,20 +995,25 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 // slot, which the look-ahead row does not touch), stored relative
                 // to the writer's pressure part (p_base), added back here with the
                 // writer's p; the writer's phi decodes f in the collision
-                float2 wr[9];
+                // (and h stored relative to the writer's c1, c2, decoded here)
                 const float2* pb2 = reinterpret_cast<const float2*>(g.pb_in);
+                auto take = [&](int i, long long k) {
+                    const float2 w = ld<CG>(pb2 + k);
+                    if (i < QS) {
+                        const uint32_t cw = ld<CG>(pb_c + k);
+                        h1d[i] = fmaf(bwq<float, QS>(i), half_lo(cw), cur.H1(i));
+                        h2d[i] = fmaf(bwq<float, QS>(i), half_hi(cw), cur.H2(i));
+                    }
+                    fd[i] = f_dec(cur.F(i), i, w.y);
+                    gp[i] = g_value<T>(R(cur.G(i))) + p_base<R>(i, R(w.x));
+                };
                 if (inner && x >= 1 && x <= g.nx - 2) {
-                    const float2* c = pb2 + (long long)y * pb_row + x;
+                    const long long c = (long long)y * pb_row + x;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(c + (-cy(i) * pb_row - cx(i)));
+                    for (int i = 0; i < 9; ++i) take(i, c + (-cy(i) * pb_row - cx(i)));
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) wr[i] = ld<CG>(pb2 + pb_src(g, pcol, y, i, inner));
-                }
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    gp[i] = g_value<T>(R(hi16<T>(s_cur[y & 1][i * W + tid]))) + p_base<R>(i, R(wr[i].x));
-                    phw[i] = wr[i].y;
+                    for (int i = 0; i < 9; ++i) take(i, pb_src(g, pcol, y, i, inner));
                 }
             }
             // ---- c. stencils (Eqs. 41-42, D2Q9 weights) from the shared ring ----
@@ -1078,16 +1132,26 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 // stochastic-rounding seed of this node and step (16-bit storage only)
                 const uint32_t key =
                     IsHalf<T>::value ? mix32(((uint32_t)y * 0x01000193u + (uint32_t)x) ^ __float_as_uint(float(p)) ^
-                                             (__float_as_uint(float(ux)) * 0x2545f491u))
+                                             (__float_as_uint(float(ux)) * 0x2545f491u) ^ (tstep * 0x9e3779b1u))
                                      : 0u;
 
                 // ---- e1. f (Eqs. 23-25) ----
+                // 16-bit storage: this node's bases, written beside its populations,
+                // which are stored relative to them: p, phi in FP32, c1, c2 rounded
+                // to half
+                uint32_t cbase = 0u;
+                R c1r = R(0), c2r = R(0);
+                if constexpr (PAIRED) {
+                    cbase = half_pair(float(c1), float(c2));
+                    c1r = R(half_lo(cbase));
+                    c2r = R(half_hi(cbase));
+                }
                 float fv[9];  // 16-bit storage: f* to store, rounded with g*
                 {
                     const R sharp = C.force_f * C.four_over_W * phi * omp;
                     const R Bx = (R(3) * (C.omega_f * phi * ux + C.force_f * dpux) + sharp * nxv);
                     const R By = (R(3) * (C.omega_f * phi * uy + C.force_f * dpuy) + sharp * nyv);
-                    if constexpr (PAIRED) collide_f16<T, R, QS>(fv, cur, phw, phi, C.omega_f, Bx, By);
+                    if constexpr (PAIRED) collide_f16<R>(fv, fd, phi, C.omega_f, Bx, By);
                     else collide_f<T, R>(o, cur.f, s_phi[y & 3][X], phi, C.omega_f, Bx, By);
                 }
                 // ---- e2. g (Eqs. 28-31) ----
@@ -1120,8 +1184,11 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                         }
                     }
                 }
-                if constexpr (PAIRED)
-                    reinterpret_cast<float2*>(g.pb_out)[(long long)y * pb_row + x] = make_float2(float(p), float(phi));
+                if constexpr (PAIRED) {
+                    const long long k = (long long)y * pb_row + x;
+                    reinterpret_cast<float2*>(g.pb_out)[k] = make_float2(float(p), float(phi));
+                    reinterpret_cast<uint32_t*>(g.pb_out + 2LL * g.ny * pb_row)[k] = cbase;
+                }
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
                 if constexpr (ONE) {
                     // ---- e3'. h3: one-scalar model (Sec. III D) ----
@@ -1176,21 +1243,33 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     const R B2x = (R(3) * (C.omega_h2 * c2 * ux + C.force_h2 * d2ux) - t2 * nxv);
                     const R B2y = (R(3) * (C.omega_h2 * c2 * uy + C.force_h2 * d2uy) - t2 * nyv);
                     const R k1 = R(1) - C.omega_h1, k2 = R(1) - C.omega_h2;
+                    // the pulled h (16-bit storage: decoded with the writers' c)
+                    auto h1 = [&](int i) -> R {
+                        if constexpr (PAIRED) return R(h1d[i]);
+                        else return cur.H1(i);
+                    };
+                    auto h2 = [&](int i) -> R {
+                        if constexpr (PAIRED) return R(h2d[i]);
+                        else return cur.H2(i);
+                    };
                     R P1 = R(0), P2 = R(0), s1 = R(0), s2 = R(0);
 #pragma unroll
                     for (int i = 0; i < QS; ++i) {
-                        P1 += cur.H1(i);
-                        P2 += cur.H2(i);
+                        P1 += h1(i);
+                        P2 += h2(i);
                     }
 #pragma unroll
                     for (int i = 1; i < QS; ++i) {
                         const R w = wq<R, QS>(i);
                         const R c1B = (cx(i) ? R(cx(i)) * B1x : R(0)) + (cy(i) ? R(cy(i)) * B1y : R(0));
                         const R c2B = (cx(i) ? R(cx(i)) * B2x : R(0)) + (cy(i) ? R(cy(i)) * B2y : R(0));
-                        const R v1 = k1 * cur.H1(i) + w * (a1 + c1B);
-                        const R v2 = k2 * cur.H2(i) + w * (a2 + c2B);
+                        const R v1 = k1 * h1(i) + w * (a1 + c1B);
+                        const R v2 = k2 * h2(i) + w * (a2 + c2B);
                         if constexpr (PAIRED) {
-                            const uint32_t wv = round_pair<T>(float(v1), float(v2), sr_word(key, float(v1), 9 + i));
+                            // stored relative to this node's c1, c2 bases
+                            const float e1 = float(v1) - bwq<float, QS>(i) * float(c1r);
+                            const float e2 = float(v2) - bwq<float, QS>(i) * float(c2r);
+                            const uint32_t wv = round_pair<T>(e1, e2, sr_word(key, e1, 9 + i));
                             s1 += lo16<T>(wv);
                             s2 += hi16<T>(wv);
                             stcs(ow + (9 + i) * 32, wv);
@@ -1205,10 +1284,14 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                     // post-collision sums: with c1 = P1 + S1/2 (Eq. 37) the BGK update gives
                     // sum h1* = P1 + S1 - Ht and sum h2* = P2 - S1 + Ht exactly; written
                     // without c1 they cannot inherit its rounding, and P1 + P2 is kept
-                    const R r1 = (P1 + (S1 - Ht)) - s1, r2 = (P2 - (S1 - Ht)) - s2;
+                    // (16-bit storage: s1, s2 sum the stored remainders, whose bases
+                    // bq_i c1r, bq_i c2r sum to the bases c1r, c2r)
                     if constexpr (PAIRED) {
-                        stcs(ow + 9 * 32, round_pair<T>(float(r1), float(r2), sr_word(key, float(r1), 9)));
+                        const float r1 = float(((P1 - c1r) + (S1 - Ht)) - s1);
+                        const float r2 = float(((P2 - c2r) - (S1 - Ht)) - s2);
+                        stcs(ow + 9 * 32, round_pair<T>(r1, r2, sr_word(key, r1, 9)));
                     } else {
+                        const R r1 = (P1 + (S1 - Ht)) - s1, r2 = (P2 - (S1 - Ht)) - s2;
                         stcs(o + 18 * 32, store_value<T>(r1));
                         stcs(o + (18 + QS) * 32, store_value<T>(r2));
                     }
@@ -1237,6 +1320,12 @@ __global__ void __launch_bounds__(STRIP_W, IsHalf<T>::value ? STRIP_MIN_BLOCKS_1
 // first step's read returns f_i = f_i^eq (Eq. 24), g_i = g_i^eq (Eqs. 29-30) and
 // h_k,i = h_k,i^eq (Eq. 35) -/+ w_i S/2, so that Eq. (37) gives back c_k.
 // With u = 0, p = 0: f_i = w_i phi, g_i = 0, h_k,i = w_i (c_k -/+ S/2).
+// 16-bit storage: the (c1, c2) half pair that node (x, y) writes among the
+// bases of its initial populations (as the step kernel would)
+__device__ __forceinline__ uint32_t init_cbase(const InitFields& in, const Geometry& g, int x, int y) {
+    const size_t k = (size_t)y * g.nx + x;
+    return half_pair(float(in.c1[k]), float(in.c2[k]));
+}
 template <typename T, typename R, int QS>
 __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ prev, Geometry g,
                             Coeffs<R> C) {
@@ -1262,15 +1351,19 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
         const R s = w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         R v = (i == 0 ? R(3) * p * (w - R(1)) : R(3) * p * w) + rho * s;
         if constexpr (IsHalf<T>::value) {
-            // relative to the pressure part of the node this slot is pulled from
+            // relative to the pressure base of the node this slot is pulled from
             int sx, sy;
             pull_src(g, x, y, i, sx, sy);
             v -= p_base<R>(i, in.p ? R(in.p[(size_t)sy * g.nx + sx]) : R(0));
         }
         put(9, i, g_stored<T>(v));
     }
-    if constexpr (IsHalf<T>::value)
-        reinterpret_cast<float2*>(g.pb_out)[(size_t)y * g.nxb * 32 + x] = make_float2(float(p), float(phi));
+    if constexpr (IsHalf<T>::value) {
+        const size_t kb = (size_t)y * g.nxb * 32 + x, N = (size_t)g.ny * g.nxb * 32;
+        reinterpret_cast<float2*>(g.pb_out)[kb] = make_float2(float(p), float(phi));
+        reinterpret_cast<uint32_t*>(g.pb_out + 2 * N)[kb] = init_cbase(in, g, x, y);
+        if (x == 0 && y == 0) reinterpret_cast<uint32_t*>(g.pb_out)[3 * N] = 0u;  // step counter
+    }
     if constexpr (PhaseFix<T>::on) {
         // the collision's rest-population rule: sum_i F_i = round((phi - 1/2) 2^31),
         // taken from the input in double so that the phase field's total is exact
@@ -1320,8 +1413,17 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
     }
     for (int i = 0; i < QS; ++i) {
         const R w = wq<R, QS>(i), e = R(1) + R(3) * cu_of(i);
-        put(18, i, w * (c1 * e - R(0.5) * S1));
-        put(18 + QS, i, w * (c2 * e + R(0.5) * S1));
+        R v1 = w * (c1 * e - R(0.5) * S1), v2 = w * (c2 * e + R(0.5) * S1);
+        if constexpr (IsHalf<T>::value) {
+            // relative to the c1, c2 bases of the node this slot is pulled from
+            int sx, sy;
+            pull_src(g, x, y, i, sx, sy);
+            const uint32_t cw = init_cbase(in, g, sx, sy);
+            v1 -= bwq<R, QS>(i) * R(half_lo(cw));
+            v2 -= bwq<R, QS>(i) * R(half_hi(cw));
+        }
+        put(18, i, v1);
+        put(18 + QS, i, v2);
     }
     pp[96] = c1;
     pp[128] = c2;
@@ -1354,6 +1456,12 @@ __global__ void __launch_bounds__(RED_THREADS)
         for (int i = 0; i < QS; ++i)
             c += pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
                  (g.one_scalar ? 0.0 : pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i));
+        // ... and its c1_w, c2_w of the slots of its h
+        if constexpr (IsHalf<T>::value) {
+            const long long N = (long long)g.ny * g.nxb * 32;
+            const uint32_t cw = reinterpret_cast<const uint32_t*>(g.pb_in + 2 * N)[(long long)y * g.nxb * 32 + x];
+            c += double(half_lo(cw)) + double(half_hi(cw));
+        }
         b += c;
     }
     __shared__ double sa[RED_THREADS / 32], sb[RED_THREADS / 32];

@@ -51,6 +51,12 @@ __global__ void __launch_bounds__(NA_THREADS)
         for (int i = 0; i < QS; ++i)
             b += lbm::pull_any<NQ, T, double>(pop, g, x, y, 18, i) +
                  (g.one_scalar ? 0.0 : lbm::pull_any<NQ, T, double>(pop, g, x, y, 18 + QS, i));
+        // ... and their c1, c2 (the bases of the stored h)
+        if constexpr (lbm::IsHalf<T>::value) {
+            const long long N = (long long)g.ny * g.nxb * 32;
+            const uint32_t cw = reinterpret_cast<const uint32_t*>(g.pb_in + 2 * N)[(long long)y * g.nxb * 32 + x];
+            b += double(lbm::half_lo(cw)) + double(lbm::half_hi(cw));
+        }
     }
     __shared__ double sa[NA_THREADS], sb[NA_THREADS];
     __shared__ long long si[NA_THREADS];
@@ -158,10 +164,11 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     const size_t elem = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32 ? 4 : 2);
     const size_t pop_bytes = (size_t)params->ny * nxb * lbm::nq_of(qs) * 32 * elem;
     if (state_bytes < pop_bytes) return na_fail(err, err_len, LBM_ERR_ARG, "state smaller than the populations of these parameters");
-    // 16-bit storage: the writers' (p, phi) pairs follow the populations and the
-    // previous-step macros (lbm_get_state's layout); phi is part of the stored f
+    // 16-bit storage: the writers' bases ((p, phi) FP32 pairs, then (c1, c2)
+    // half pairs) follow the populations and the previous-step macros
+    // (lbm_get_state's layout); phi, c1 and c2 are part of the stored f and h
     const size_t pb_off = pop_bytes + (size_t)params->ny * nxb * 5 * 32 * sizeof(float);
-    const size_t pb_bytes = elem == 2 ? (size_t)params->ny * nxb * 32 * 2 * sizeof(float) : 0;
+    const size_t pb_bytes = elem == 2 ? (size_t)params->ny * nxb * 32 * 12 + 8 : 0;  // bases, step counter
     if (elem == 2 && state_bytes < pb_off + pb_bytes)
         return na_fail(err, err_len, LBM_ERR_ARG, "16-bit state smaller than lbm_state_bytes() of these parameters");
 

@@ -62,11 +62,11 @@ def test_workspace_size_and_validation(L):
     base = 2 * 28 * 4 * 1024 * 2048 + 5 * 4 * 1024 * 2048
     assert base <= n < base + 65536
     # 16-bit population storage: half the population bytes, FP32 macros, and
-    # two planes of the writers' (p, phi) pairs the populations are stored against
+    # two planes of the writers' (p, phi, c1, c2) bases the populations are stored against
     for prec in ("bf16", "fp16"):
         p16 = lbm.make_params(dict(nx=1024, ny=2048), prec)
         n16 = L.lbm_workspace_bytes(ctypes.byref(p16))
-        base16 = 2 * 28 * 2 * 1024 * 2048 + 5 * 4 * 1024 * 2048 + 2 * 8 * 1024 * 2048
+        base16 = 2 * 28 * 2 * 1024 * 2048 + 5 * 4 * 1024 * 2048 + 2 * 12 * 1024 * 2048
         assert base16 <= n16 < base16 + 65536
     bad = [dict(nx=0, ny=4), dict(nx=4, ny=4, scalar_q=7), dict(nx=4, ny=4, rho1=-1.0),
            dict(nx=4, ny=4, D2=0.0), dict(nx=4, ny=4, M=0.0), dict(nx=4, ny=4, visc_model=5)]
