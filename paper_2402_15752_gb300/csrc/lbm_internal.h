@@ -36,9 +36,10 @@ constexpr int STRIP_W = 32 * STRIP_WARPS;
 constexpr int STRIP_MIN_BLOCKS = LBM_STRIP_MIN_BLOCKS;  // occupancy target (register cap)
 // (6 CTAs = 24 warps per SM, 80 registers; FP32 fits it because the pulled
 // populations of the look-ahead row wait in shared memory.)  16-bit storage
-// has its own cap, measured separately.
+// has its own cap, measured separately: 5 CTAs per SM, 96 registers without
+// spills (6 CTAs at 80 registers spill 54 bytes and ran 2 % slower).
 #ifndef LBM_STRIP_MIN_BLOCKS_16
-#define LBM_STRIP_MIN_BLOCKS_16 6
+#define LBM_STRIP_MIN_BLOCKS_16 5
 #endif
 constexpr int STRIP_MIN_BLOCKS_16 = LBM_STRIP_MIN_BLOCKS_16;
 // FP64 arithmetic: 3 CTAs per SM (168 registers) keep it free of spills; its

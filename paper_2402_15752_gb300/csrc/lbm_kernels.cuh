@@ -832,19 +832,20 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
 #pragma unroll
         for (int i = 0; i < 9; ++i) s_hoff[tid == 0 ? 0 : 1][i] = hd[i];
     }
-    // Halo nodes with FP32 storage and at least two warps: the warp of each halo
-    // thread (the first warp: right halo; the last: left halo) loads the halo
-    // node's words one per lane, beside the lanes' own loads, and the halo
-    // thread sums them from shared memory in the same order as any node's; it
-    // then waits for one memory round trip per row instead of two.  (16-bit
-    // storage, bound by instruction issue rather than latency, measured 2 %
-    // slower with it.)
-    constexpr bool HALO_SPLIT = CUR_SMEM && !PAIRED && W >= 64;
+    // Halo nodes with at least two warps: the warp of each halo thread (the
+    // first warp: right halo; the last: left halo) loads the halo node's words
+    // one per lane, beside the lanes' own loads, and the halo thread sums them
+    // from shared memory in the same order as any node's; it then waits for one
+    // memory round trip per row instead of two.  16-bit storage adds the halo
+    // node's writers' bases (9 phase fields, QS (c1, c2) words): 28 words with
+    // the D2Q5 scalars, one per lane.
+    constexpr int NHW = PAIRED ? NWC + 9 + QS : NWC;  // words loaded for a halo node
+    constexpr bool HALO_SPLIT = CUR_SMEM && W >= 64 && NHW <= 32;
     const int wid = tid >> 5;
     const bool hwarp = wid == 0 || wid == W / 32 - 1;
     const int hkw = wid == 0 ? 0 : 1;
     const int hxw = resolve(wid == 0 ? x0 + W : x0 - 1, g.nx, g.wall_x);
-    __shared__ uint32_t s_hpop[2][HALO_SPLIT ? NWC : 1];
+    __shared__ uint32_t s_hpop[2][HALO_SPLIT ? NHW : 1];
     int hoffk = 0;       // this lane's word of the halo node, relative to the node
     bool hload = false;  // whether this lane loads one
     if constexpr (HALO_SPLIT) {
@@ -861,6 +862,13 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             }
             hoffk = s_hoff[hkw][dir] + plane * 32;
             hload = !(ONE && !PAIRED && k >= 9 + QS);  // one-scalar model: no h2
+        }
+        if (PAIRED && hwarp && k >= NWC && k < NHW) {
+            // a base of the writer of direction i of the halo node: its index in
+            // the bases planes relative to the row's first node (rows 1 .. ny - 2)
+            const int i = k < NWC + 9 ? k - NWC : k - NWC - 9;
+            hoffk = (int)pb_src(g, pb_col(g, hxw), 0, i, true);
+            hload = true;
         }
     }
 
@@ -902,7 +910,15 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         if (y_in) {
             pull_fh_fast<QS, T, R, CG, ONE>(src, node_off<NQL>(g, rx, ry), doff, P);
             if constexpr (HALO_SPLIT) {
-                if (hload) hv = ld<CG>(reinterpret_cast<const uint32_t*>(src) + node_off<NQL>(g, hxw, ry) + hoffk);
+                if (hload) {
+                    if (lane < NWC) {
+                        hv = ld<CG>(reinterpret_cast<const uint32_t*>(src) + node_off<NQL>(g, hxw, ry) + hoffk);
+                    } else if constexpr (PAIRED) {
+                        // writer of direction i of the halo node: its phase field, then its (c1, c2)
+                        const long long k = (long long)ry * pb_row + hoffk;
+                        hv = lane < NWC + 9 ? __float_as_uint(ld<CG>(g.pb_in + 2 * k + 1)) : ld<CG>(pb_c + k);
+                    }
+                }
             }
         } else {
             pull_fh_any<QS, T, R, CG, ONE>(src, g, rx, ry, P);
@@ -920,14 +936,28 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
         if constexpr (HALO_SPLIT) {
             if (hwarp && y_in) {
                 __syncwarp();  // the halo thread has read the previous row's words
-                if (lane < NWC) s_hpop[hkw][lane] = hv;
+                if (lane < NHW) s_hpop[hkw][lane] = hv;
                 __syncwarp();
                 if (halo) {
                     NodeFH<T, R, QS> hp;
                     hp.load(s_hpop[hkw], 1);
                     PS hs;
                     R a, b, c;
-                    zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
+                    if constexpr (PAIRED) {
+                        // the bases in writer_bases' order
+                        float hphs[9], hc1 = 0.0f, hc2 = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) hphs[i] = __uint_as_float(s_hpop[hkw][NWC + i]);
+#pragma unroll
+                        for (int i = 0; i < QS; ++i) {
+                            const uint32_t cw = s_hpop[hkw][NWC + 9 + i];
+                            hc1 = fmaf(bwq<float, QS>(i), half_lo(cw), hc1);
+                            hc2 = fmaf(bwq<float, QS>(i), half_hi(cw), hc2);
+                        }
+                        zeroth_b<T, R, QS, ONE>(C, hp, hphs, hc1, hc2, hs, a, b, c);
+                    } else {
+                        zeroth<T, R, QS, ONE>(C, hp, hs, a, b, c);
+                    }
                     s_phi[yy & 3][hcol] = hs;
                     s_c[yy & 3][0][hcol] = b;
                     s_c[yy & 3][1][hcol] = c;
