@@ -245,6 +245,10 @@ struct lbm_batch {
         }
         if (e == cudaSuccess && g) e = cudaGraphInstantiate(&graph, g, 0);
         if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess && graph) {
+            e = cudaGraphUpload(graph, stream);  // now, not at the first launch
+            if (e != cudaSuccess) cudaGraphExecDestroy(graph);
+        }
         if (e != cudaSuccess) { graph = nullptr; cudaGetLastError(); }
         cudaStreamDestroy(cap);
     }

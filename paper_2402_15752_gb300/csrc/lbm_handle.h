@@ -164,6 +164,9 @@ struct lbm_handle {
         if (e != cudaSuccess) return e;
         e = cudaGraphInstantiate(&graph[parity][level], g, 0);
         cudaGraphDestroy(g);
+        // upload now rather than at the first launch, which may be inside a
+        // caller's timed region
+        if (e == cudaSuccess) e = cudaGraphUpload(graph[parity][level], stream);
         return e;
     }
     // Every level for both starting buffers, on the first call that steps at
