@@ -45,6 +45,8 @@ extern "C" {
 #define LBM_ERR_CUDA         (-4) /* a CUDA runtime call failed                       */
 #define LBM_ERR_NONFINITE    (-5) /* a NaN/Inf macro value was produced by a step     */
 #define LBM_ERR_TIMEOUT      (-6) /* a bounded device wait gave up (batched runner)   */
+#define LBM_ERR_BOUNDS       (-7) /* debug build only: an access fell outside the
+                                     workspace (it was skipped, see lbm_debug_build) */
 
 /* ---- enums ---- */
 #define LBM_BC_PERIODIC 0
@@ -191,8 +193,24 @@ int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_devic
 int lbm_conserved(lbm_handle* h, double out[2]);
 
 /* Synchronise the stream and report LBM_ERR_NONFINITE if any finished step
- * produced a NaN/Inf; clears nothing. */
+ * produced a NaN/Inf; clears nothing.  A debug build first reports
+ * LBM_ERR_BOUNDS if a checked access failed since the last lbm_sync of any
+ * handle (that check is cleared by the report). */
 int lbm_sync(lbm_handle* h);
+
+/* 1 if this library is the debug build (compiled with LBM_DEBUG=1), else 0.
+ * In the debug build the step, field and reduction kernels check every global
+ * load and store of the workspace against the handle's workspace range (the
+ * state's range for lbm_conserved_noalloc); an access outside it is skipped (a
+ * load reads zero), recorded, and reported by lbm_sync as LBM_ERR_BOUNDS.
+ * Nothing faults or traps.  A development aid, not in the paper. */
+int lbm_debug_build(void);
+
+/* Debug build only (LBM_ERR_ARG otherwise): check the handle's kernels against
+ * the first `bytes` of its workspace instead of all of it (bytes <= the
+ * workspace size), so that a test can show an access beyond the range being
+ * skipped and reported.  Synchronises the stream and drops the captured graphs. */
+int lbm_debug_limit_workspace(lbm_handle* h, size_t bytes);
 
 /* Checkpoint: the populations and previous-step macros of the current state,
  * and with 16-bit storage the (p, phi) FP32 and (c1, c2) half bases of every node that the stored

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <new>
 #include <type_traits>
+#include <vector>
 
 using lbm::detail::DeviceGuard;
 using lbm::detail::Layout;
@@ -158,6 +159,23 @@ static int choose_strip_height(const lbm_handle* h) {
     return best_h;
 }
 
+// Debug build: the readers of the status words of every translation unit with
+// checked kernels (registered during static initialisation).
+namespace lbm {
+namespace {
+std::vector<unsigned (*)()>& debug_readers() {
+    static std::vector<unsigned (*)()> readers;
+    return readers;
+}
+}  // namespace
+void register_debug_status(unsigned (*take)()) { debug_readers().push_back(take); }
+unsigned debug_status_take() {
+    unsigned v = 0;
+    for (auto take : debug_readers()) v |= take();
+    return v;
+}
+}  // namespace lbm
+
 extern "C" {
 
 size_t lbm_workspace_bytes(const lbm_params* params) {
@@ -202,6 +220,8 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
     h->device = attr.device;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->ws = static_cast<uint8_t*>(d_workspace);
+    h->geo.ws_lo = reinterpret_cast<const char*>(h->ws);
+    h->geo.ws_hi = h->geo.ws_lo + L.total;
     DeviceGuard dg(h->device);
     cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming);
@@ -349,12 +369,28 @@ int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_devic
     return LBM_OK;
 }
 
+int lbm_debug_build(void) { return LBM_DEBUG; }
+
+int lbm_debug_limit_workspace(lbm_handle* h, size_t bytes) {
+    if (!h) return LBM_ERR_ARG;
+    if (!LBM_DEBUG) return h->fail(LBM_ERR_ARG, "lbm_debug_limit_workspace needs the debug build");
+    if (bytes > h->L.total) return h->fail(LBM_ERR_ARG, "the checked range cannot exceed the workspace");
+    DeviceGuard dg(h->device);
+    const cudaError_t e = cudaStreamSynchronize(h->stream);  // no launch in flight uses the old range
+    if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_debug_limit_workspace", e);
+    h->geo.ws_hi = h->geo.ws_lo + bytes;
+    h->drop_graphs();  // they were captured with the old range
+    return LBM_OK;
+}
+
 int lbm_sync(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
     DeviceGuard dg(h->device);
     cudaError_t e = cudaMemcpyAsync(h->h_status, h->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_sync", e);
+    if (LBM_DEBUG && lbm::debug_status_take() != 0u)
+        return h->fail(LBM_ERR_BOUNDS, "debug build: a kernel access fell outside the workspace (skipped)");
     h->status_pending = false;
     if (*h->h_status) h->nonfinite = true;
     if (h->nonfinite) return h->fail(LBM_ERR_NONFINITE, "a step produced a non-finite macro value");
@@ -412,8 +448,7 @@ void lbm_destroy(lbm_handle* h) {
     {
         DeviceGuard dg(h->device);
         if (h->stream || h->capture) cudaStreamSynchronize(h->stream);
-        for (auto& row : h->graph)
-            for (auto& g : row) if (g) cudaGraphExecDestroy(g);
+        h->drop_graphs();
         if (h->status_ev) cudaEventDestroy(h->status_ev);
         if (h->capture) cudaStreamDestroy(h->capture);
         if (h->h_status) cudaFreeHost(h->h_status);

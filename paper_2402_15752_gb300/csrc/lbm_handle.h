@@ -169,6 +169,14 @@ struct lbm_handle {
         if (e == cudaSuccess) e = cudaGraphUpload(graph[parity][level], stream);
         return e;
     }
+    void drop_graphs() {
+        for (auto& row : graph)
+            for (auto& g : row)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
+    }
     // Every level for both starting buffers, on the first call that steps at
     // least twice, so that later calls of any length launch no capture.
     cudaError_t build_graphs() {

@@ -71,7 +71,26 @@ struct Geometry {
     // planes alternate with the population buffers.
     const float* pb_in;
     float* pb_out;
+    // The device memory the step may touch: the handle's workspace (or the
+    // state given to lbm_conserved_noalloc).  Read only by an LBM_DEBUG build,
+    // whose step kernel checks every global access against it.
+    const char* ws_lo;
+    const char* ws_hi;
 };
+
+// Debug build (compiled with -DLBM_DEBUG=1): the step kernel checks every
+// global load and store of the workspace against Geometry::ws_lo .. ws_hi; an
+// access outside sets FLAG_BOUNDS in a device status word and is skipped (a
+// load returns zero), so a bad index is reported and never faults.
+#ifndef LBM_DEBUG
+#define LBM_DEBUG 0
+#endif
+constexpr unsigned FLAG_BOUNDS = 2u;
+// Debug build: the OR of FLAG_BOUNDS of every checked kernel since the last
+// read; cleared by the read (0 in a release build).  Each translation unit
+// with checked kernels registers the reader of its own status word.
+unsigned debug_status_take();
+void register_debug_status(unsigned (*take)());
 
 // Model variant of the step kernel: bit 0 one-scalar, bits 1-2 gradient scheme.
 inline int variant_of(const Geometry& g) { return (g.one_scalar ? 1 : 0) | (g.grad_scheme << 1); }

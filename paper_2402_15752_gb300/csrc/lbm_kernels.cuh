@@ -79,24 +79,80 @@ __device__ __forceinline__ float three_fifths(float s) {
 }
 __device__ __forceinline__ double three_fifths(double s) { return 0.6 * s; }
 
-template <typename T>
-__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 // Population / macro loads of the step: through the read-only path when the
 // buffer is constant for the kernel's lifetime (one step per launch), or cached
 // in L2 only (CG) when other CTAs of the same launch rewrite it between steps
 // (the persistent batched kernel), so that no stale L1 line is read.
+#if LBM_DEBUG
+// Debug build: the range a CTA's accesses must fall in (set by dbg_begin) and
+// the status word a failed check reports to: a device global of this
+// translation unit (always a valid address, whatever the CTA's range holds),
+// read and cleared by the host through debug_status_take.
+__shared__ const char* dbg_lo;
+__shared__ const char* dbg_hi;
+static __device__ unsigned dbg_status;
+namespace {
+unsigned dbg_status_take_here() {
+    unsigned v = 0;
+    const unsigned zero = 0;
+    if (cudaMemcpyFromSymbol(&v, dbg_status, sizeof v) != cudaSuccess) v = FLAG_BOUNDS;
+    cudaMemcpyToSymbol(dbg_status, &zero, sizeof zero);
+    return v;
+}
+const bool dbg_registered = (register_debug_status(dbg_status_take_here), true);
+}  // namespace
+#endif
+// Whole CTA, at the start of a kernel that loads through ld / stores through
+// st_chk and stcs: its range of device memory (a no-op in a release build).
+__device__ __forceinline__ void dbg_begin(const char* lo, const char* hi) {
+#if LBM_DEBUG
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        dbg_lo = lo;
+        dbg_hi = hi;
+    }
+    __syncthreads();
+#endif
+}
+// Whether an access of n bytes at p is inside the CTA's range (always in a
+// release build); outside, FLAG_BOUNDS is reported and the caller skips it.
+__device__ __forceinline__ bool dbg_in(const void* p, size_t n) {
+#if LBM_DEBUG
+    const char* c = static_cast<const char*>(p);
+    if (c >= dbg_lo && c + n <= dbg_hi) return true;
+    atomicOr(&dbg_status, FLAG_BOUNDS);
+    return false;
+#else
+    (void)p;
+    (void)n;
+    return true;
+#endif
+}
 template <bool CG, typename T>
 __device__ __forceinline__ T ld(const T* p) {
+    if (!dbg_in(p, sizeof(T))) return T{};
     if constexpr (CG) return __ldcg(p);
     else return __ldg(p);
 }
+// a plain load and a plain store of the workspace, checked in a debug build
+// (for data the kernel itself rewrites, which the read-only path may not cache)
 template <typename T>
-__device__ __forceinline__ void stcs(T* p, T v) { __stcs(p, v); }
+__device__ __forceinline__ T ld_plain(const T* p) {
+    if (!dbg_in(p, sizeof(T))) return T{};
+    return *p;
+}
+template <typename T>
+__device__ __forceinline__ void st_chk(T* p, T v) {
+    if (dbg_in(p, sizeof(T))) *p = v;
+}
+template <typename T>
+__device__ __forceinline__ void stcs(T* p, T v) {
+    if (dbg_in(p, sizeof(T))) __stcs(p, v);
+}
 __device__ __forceinline__ void stcs(__half* p, __half v) {
-    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
+    if (dbg_in(p, sizeof v)) __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
 }
 __device__ __forceinline__ void stcs(__nv_bfloat16* p, __nv_bfloat16 v) {
-    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+    if (dbg_in(p, sizeof v)) __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
 }
 
 // Storage <-> arithmetic conversions (16-bit storage rounds to nearest even).
@@ -780,6 +836,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     constexpr int NWC = CUR_SMEM ? NodeFH<T, R, QS>::NW : 1;
     __shared__ uint32_t s_cur[2][NWC * W];
 
+    dbg_begin(g.ws_lo, g.ws_hi);  // debug build: the range every global access is checked against
     const int tid = threadIdx.x, lane = tid & 31;
     const int x = x0 + tid;
     const bool col_in = x < g.nx;
@@ -823,7 +880,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
     if constexpr (PAIRED) {
         const long long cnt = 3LL * g.ny * pb_row;  // in 4-byte words
         tstep = ld<CG>(reinterpret_cast<const uint32_t*>(g.pb_in) + cnt);
-        if (!FIELDS && x0 == 0 && ya == 0 && tid == 0) reinterpret_cast<uint32_t*>(g.pb_out)[cnt] = tstep + 1u;
+        if (!FIELDS && x0 == 0 && ya == 0 && tid == 0) st_chk(reinterpret_cast<uint32_t*>(g.pb_out) + cnt, tstep + 1u);
     }
     __shared__ int s_hoff[2][9];  // the halo nodes' offsets
     if (halo) {
@@ -1010,7 +1067,7 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
             if constexpr (!FIELDS || GS == 2) {
                 const R* pp = prev + node_off<5>(g, x, y);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) pv[k] = CG ? __ldcg(pp + k * 32) : pp[k * 32];
+                for (int k = 0; k < 5; ++k) pv[k] = CG ? ld<true>(pp + k * 32) : ld_plain(pp + k * 32);
             }
         }
         // ---- b. zeroth moments of row y+1 (f, h1, h2 pulled once per node) ----
@@ -1141,11 +1198,11 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 {
                     // one-scalar model: the c1 slot holds c = c1 + c2, the c2 slot 0
                     R* pp = prev + node_off<5>(g, x, y);
-                    pp[0] = phi;
-                    pp[32] = ux;
-                    pp[64] = uy;
-                    pp[96] = ONE ? c1 + c2 : c1;
-                    pp[128] = ONE ? R(0) : c2;
+                    st_chk(pp, phi);
+                    st_chk(pp + 32, ux);
+                    st_chk(pp + 64, uy);
+                    st_chk(pp + 96, ONE ? c1 + c2 : c1);
+                    st_chk(pp + 128, ONE ? R(0) : c2);
                 }
                 // non-finite values, or phi outside the fixed-point range
                 // (16-bit storage also checks p: rounding a NaN population can lose
@@ -1216,8 +1273,8 @@ __device__ __forceinline__ void strip_tile(const T* __restrict__ src, T* __restr
                 }
                 if constexpr (PAIRED) {
                     const long long k = (long long)y * pb_row + x;
-                    reinterpret_cast<float2*>(g.pb_out)[k] = make_float2(float(p), float(phi));
-                    reinterpret_cast<uint32_t*>(g.pb_out + 2LL * g.ny * pb_row)[k] = cbase;
+                    st_chk(reinterpret_cast<float2*>(g.pb_out) + k, make_float2(float(p), float(phi)));
+                    st_chk(reinterpret_cast<uint32_t*>(g.pb_out + 2LL * g.ny * pb_row) + k, cbase);
                 }
                 // ---- e3. h1, h2 (Eqs. 34-36) ----
                 if constexpr (ONE) {
@@ -1464,6 +1521,7 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
 template <typename T, int QS>
 __global__ void __launch_bounds__(RED_THREADS)
     conserved_partials(const T* __restrict__ pop, Geometry g, double* __restrict__ partials) {
+    dbg_begin(g.ws_lo, g.ws_hi);
     constexpr int NQ = nq_of(QS);
     // fixed point: sum of the integers Phi (exact); otherwise sum of phi
     long long ai = 0;

@@ -32,6 +32,7 @@ double* na_addr[NA_MAX_DEVICES] = {};  // device address of na_scratch, per devi
 template <typename T, int QS>
 __global__ void __launch_bounds__(NA_THREADS)
     na_chunk_partials(const T* __restrict__ pop, lbm::Geometry g, double* __restrict__ part) {
+    lbm::dbg_begin(g.ws_lo, g.ws_hi);  // debug build: the caller's state is the whole range
     constexpr int NQ = lbm::nq_of(QS);
     const long long n = (long long)g.nx * g.ny;
     const long long k0 = blockIdx.x * NA_CHUNK, k1 = min(k0 + NA_CHUNK, n);
@@ -213,6 +214,8 @@ extern "C" int lbm_conserved_noalloc(const lbm_params* params, const void* d_sta
     g.grad_scheme = params->grad_scheme;
     g.pb_in = elem == 2 ? reinterpret_cast<const float*>(static_cast<const uint8_t*>(d_state) + pb_off) : nullptr;
     g.pb_out = nullptr;
+    g.ws_lo = static_cast<const char*>(d_state);
+    g.ws_hi = g.ws_lo + state_bytes;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = lbm::by_storage(params->precision, [&](auto t, auto) {
         return na_launch<decltype(t)>(d_state, g, qs, scratch, (int)nchunks, s);

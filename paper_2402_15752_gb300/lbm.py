@@ -13,7 +13,9 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblbm.so")
+# LBM_DEBUG=1 in the environment selects the debug build (liblbm_debug.so:
+# every kernel access of the workspace checked, lbm_sync reports LBM_ERR_BOUNDS)
+LIB_PATH = os.path.join(_PKG, "liblbm_debug.so" if os.environ.get("LBM_DEBUG") == "1" else "liblbm.so")
 
 # ---- constants mirrored from include/lbm.h ----
 LBM_OK = 0
@@ -23,8 +25,10 @@ LBM_ERR_WORKSPACE = -3
 LBM_ERR_CUDA = -4
 LBM_ERR_NONFINITE = -5
 LBM_ERR_TIMEOUT = -6
+LBM_ERR_BOUNDS = -7
 ERROR_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_UNSTABLE_TAU", -3: "LBM_ERR_WORKSPACE",
-               -4: "LBM_ERR_CUDA", -5: "LBM_ERR_NONFINITE", -6: "LBM_ERR_TIMEOUT"}
+               -4: "LBM_ERR_CUDA", -5: "LBM_ERR_NONFINITE", -6: "LBM_ERR_TIMEOUT",
+               -7: "LBM_ERR_BOUNDS"}
 
 LBM_BC_PERIODIC, LBM_BC_WALL = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP32_BF16STORE, LBM_FP32_FP16STORE = 0, 1, 2, 3
@@ -85,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbm_get_fields": (ctypes.c_int, [vp, ctypes.c_uint32, dp, i32, i32]),
         "lbm_conserved": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "lbm_sync": (ctypes.c_int, [vp]),
+        "lbm_debug_build": (ctypes.c_int, []),
+        "lbm_debug_limit_workspace": (ctypes.c_int, [vp, sz]),
         "lbm_state_bytes": (sz, [vp]),
         "lbm_get_state": (ctypes.c_int, [vp, dp, sz, i32]),
         "lbm_set_state": (ctypes.c_int, [vp, dp, sz, i32]),

@@ -36,6 +36,17 @@ def test_every_declared_function_is_exported(L):
         assert hasattr(L, n), n
 
 
+def test_debug_build_exports_the_same_functions(L):
+    """The debug build (kernels bounds-checked) loads without a GPU, exports every
+    declared function and says which build it is; the release build says 0."""
+    from paper_2402_15752_gb300 import build
+    D = ctypes.CDLL(build.build(debug=True))
+    for n in declared_functions():
+        assert hasattr(D, n), n
+    assert D.lbm_debug_build() == 1
+    assert L.lbm_debug_build() == 0
+
+
 def test_ctypes_struct_mirrors_the_header():
     text = open(HEADER).read()
     body = re.search(r"typedef struct \{(.*?)\} lbm_params;", text, flags=re.S).group(1)
