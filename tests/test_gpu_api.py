@@ -67,6 +67,27 @@ def test_graph_and_plain_launches_agree_bitwise():
         assert np.array_equal(fa[k], fb[k]), k
 
 
+def test_every_graph_length_matches_plain_launches():
+    """A call of n steps replays captured graphs for the binary digits of n
+    (32, 16, 8, 4, 2) and launches an odd last step plainly; the graphs are
+    captured for both starting buffers.  63 steps (every graph length and a
+    plain step, ending in the other buffer) and then 30 more (starting from
+    that buffer) give the bits of 93 single steps."""
+    w = wl.droplet64(nx=45, ny=38, R=9.0, rho2=0.4, mu2=0.05)
+    a = Simulation(w.params, precision="fp32")
+    a.init(w.sdf, 1.0, 0.2)
+    a.step(63)
+    a.step(30)
+    b = Simulation(w.params, precision="fp32")
+    b.init(w.sdf, 1.0, 0.2)
+    for _ in range(93):
+        b.step(1)
+    assert a.time == b.time == 93
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
 def test_host_and_device_readback_agree():
     w = wl.droplet64(nx=33, ny=65, R=8.0)
     sim = Simulation(w.params, precision="fp32")
