@@ -56,18 +56,19 @@ extern "C" {
 #define LBM_FP32           1 /* FP32 storage and arithmetic                      */
 /* 16-bit population storage, FP32 arithmetic: each population is read, converted
  * and collided in FP32 and rounded stochastically on the store (the random bits
- * are a hash seeded per node and step from the node's coordinates, its new macros
- * and a step counter kept in the state: deterministic, so runs and restarts are
- * reproducible).  Each node also writes
- * its pressure and phase field (FP32) and its scalars (rounded to IEEE half)
- * beside its populations, which are stored as offsets from their writer's: f_i - b_i phi_w,
- * g_i - 3 b_i p_w (g_0 - 3 (b_0 - 1) p_w) and h_k,i - bq_i c_k,w, b_i and bq_i the
- * D2Q9 and scalar-lattice weights rounded to multiples of 2^-20 so that they sum
- * to exactly 1; g in half is scaled by 2^10; the five previous-step macros stay
- * FP32.  Not in the paper: 56 population bytes per node instead of 112
- * (scalar_q = 5), plus 12 bytes of (p, phi, c1, c2), at a field
- * error of 1e-4..1e-3 (half) and 1e-3..1e-2 (bfloat16), the density-ratio-1000
- * bubble included.  A step of a 16-bit run also reports a non-finite pressure. */
+ * are a hash seeded per node and step from the node's coordinates, its new
+ * macros and a step counter kept in the state: deterministic, so runs and
+ * restarts are reproducible).  Each node also writes its pressure and phase
+ * field (FP32) and its scalars (rounded to IEEE half) beside its populations,
+ * which are stored as offsets from their writer's: f_i - b_i phi_w,
+ * g_i - 3 b_i p_w (g_0 - 3 (b_0 - 1) p_w) and h_k,i - bq_i c_k,w, with b_i and
+ * bq_i the D2Q9 and scalar-lattice weights rounded to multiples of 2^-20 so that
+ * they sum to exactly 1; g in half is scaled by 2^10; the five previous-step
+ * macros stay FP32; c1 and c2 must stay below 65504 in magnitude (their bases
+ * are halves).  Not in the paper: 56 population bytes per node instead of 112
+ * (scalar_q = 5), plus 12 bytes of (p, phi, c1, c2), at a field error of
+ * 1e-4..1e-3 (half) and 1e-3..1e-2 (bfloat16), the density-ratio-1000 bubble
+ * included.  A step of a 16-bit run also reports a non-finite pressure. */
 #define LBM_FP32_BF16STORE 2 /* bfloat16 storage (8-bit significand, FP32 range)  */
 #define LBM_FP32_FP16STORE 3 /* IEEE half storage (11-bit significand, |x| < 65504;
                                 values below 6.1e-5 lose bits as subnormals)        */

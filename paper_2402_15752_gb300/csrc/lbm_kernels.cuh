@@ -79,10 +79,6 @@ __device__ __forceinline__ float three_fifths(float s) {
 }
 __device__ __forceinline__ double three_fifths(double s) { return 0.6 * s; }
 
-// Population / macro loads of the step: through the read-only path when the
-// buffer is constant for the kernel's lifetime (one step per launch), or cached
-// in L2 only (CG) when other CTAs of the same launch rewrite it between steps
-// (the persistent batched kernel), so that no stale L1 line is read.
 #if LBM_DEBUG
 // Debug build: the range a CTA's accesses must fall in (set by dbg_begin) and
 // the status word a failed check reports to: a device global of this
@@ -127,6 +123,10 @@ __device__ __forceinline__ bool dbg_in(const void* p, size_t n) {
     return true;
 #endif
 }
+// Population / macro loads of the step: through the read-only path when the
+// buffer is constant for the kernel's lifetime (one step per launch), or cached
+// in L2 only (CG) when other CTAs of the same launch rewrite it between steps
+// (the persistent batched kernel), so that no stale L1 line is read.
 template <bool CG, typename T>
 __device__ __forceinline__ T ld(const T* p) {
     if (!dbg_in(p, sizeof(T))) return T{};
