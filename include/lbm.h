@@ -157,7 +157,9 @@ int lbm_create(const lbm_params* params, void* d_workspace, size_t workspace_byt
  * phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1_tilde * phi, c2 = c2_tilde * (1 - phi),
  * u = 0, p = 0.  Populations start at their equilibria (f_i = w_i phi, g_i = 0) and
  * h_k,i = w_i (c_k -/+ S/2) so that Eq. (37) returns the given c_k; the time counter
- * restarts at 0.  A host sdf is copied synchronously before the call returns. */
+ * restarts at 0.  A host sdf is read on the stream: page-locked (mapped) memory in
+ * place by the GPU, so keep it unchanged until the stream has passed this call;
+ * pageable memory through a copy that completes before the call returns. */
 int lbm_init(lbm_handle* h, const double* sdf, int32_t sdf_on_device,
              double c1_tilde, double c2_tilde);
 
@@ -184,7 +186,9 @@ int lbm_step(lbm_handle* h, int64_t nsteps);
  * populations, Eqs. (26), (32), (37), with the stencils of Eqs. (41)-(42)).
  * out receives popcount(mask) consecutive fields of nx*ny values, in mask-bit order,
  * as doubles (LBM_OUT_F64) or floats (LBM_OUT_F32).  out_on_device = 0: out is host
- * memory and the call synchronises the stream before returning. */
+ * memory (page-locked, mapped memory is written in place by the GPU, other memory
+ * through device staging and a copy) and the call synchronises the stream before
+ * returning. */
 int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_device,
                    int32_t out_dtype);
 

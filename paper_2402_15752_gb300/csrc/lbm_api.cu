@@ -246,6 +246,19 @@ static int init_common(lbm_handle* h, const double* phi, const double* c1, const
     return LBM_OK;
 }
 
+// Device address of a host buffer that the GPU can read and write in place
+// (page-locked memory mapped into the current device's address space; on a
+// Grace-Blackwell node over NVLink-C2C, faster than a copy-engine transfer of
+// the same bytes), or nullptr: then the call stages through device memory.
+static void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int lbm_init(lbm_handle* h, const double* sdf, int32_t sdf_on_device, double c1_tilde, double c2_tilde) {
     if (!h) return LBM_ERR_ARG;
     if (!sdf) return h->fail(LBM_ERR_ARG, "sdf is NULL");
@@ -257,8 +270,12 @@ int lbm_init(lbm_handle* h, const double* sdf, int32_t sdf_on_device, double c1_
     cudaError_t e = cudaSuccess;
     const double* src = sdf;
     if (!sdf_on_device) {
-        e = cudaMemcpyAsync(phi, sdf, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        src = phi;
+        // mapped host memory is read in place by the kernel, else copied first
+        src = static_cast<const double*>(mapped_host(sdf));
+        if (!src) {
+            e = cudaMemcpyAsync(phi, sdf, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            src = phi;
+        }
     }
     if (e == cudaSuccess) e = lbm::launch_sdf_to_fields(src, phi, c1, c2, n, h->p.W, c1_tilde, c2_tilde, h->stream);
     if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_init", e);
@@ -348,7 +365,16 @@ int lbm_get_fields(lbm_handle* h, uint32_t mask, void* out, int32_t out_on_devic
         if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_fields", e);
         return LBM_OK;
     }
-    // host output: evaluate into the idle population buffer, in batches that fit
+    // host output the GPU can write in place (mapped page-locked memory): one
+    // evaluation straight into it
+    if (void* mapped = mapped_host(out)) {
+        e = h->fields(h->cur, mask, mapped, f64, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return h->fail(LBM_ERR_CUDA, "lbm_get_fields", e);
+        return LBM_OK;
+    }
+    // other host output: evaluate into the idle population buffer, in batches
+    // that fit, and copy
     const size_t per_field = (size_t)h->p.nx * h->p.ny * (f64 ? 8 : 4);
     const size_t batch = h->L.pop_bytes / per_field;
     uint8_t* dst = static_cast<uint8_t*>(out);
