@@ -326,6 +326,12 @@ def run_ours(args, rank, world, local):
         sdf_host = torch.from_numpy(np.ascontiguousarray(w.sdf, dtype=np.float64)).pin_memory()
         out_host = torch.empty((6, w.params["ny"], w.params["nx"]), dtype=torch.float32).pin_memory()
         names = ("phi", "ux", "uy", "p", "c1", "c2")
+        # one untimed pass through the same buffers first: the device's first
+        # touches of newly page-locked host memory are a one-time cost, as the
+        # warm-up steps are for the device-timed loop
+        sim.init(sdf_host, w.c1_tilde, w.c2_tilde)
+        sim.step(max(3, args.warmup))
+        sim.fields(names=names, dtype="f32", out=out_host.numpy())
         barrier()
         torch.cuda.synchronize(dev)
         t0 = torch.cuda.Event(enable_timing=True)
@@ -453,6 +459,13 @@ def run_batched(args, rank, world, local):
         outs = [torch.empty((6, w.params["ny"], w.params["nx"]), dtype=torch.float32).pin_memory()
                 for w in cases]
         names = ("phi", "ux", "uy", "p", "c1", "c2")
+        # one untimed pass through the same buffers first (first touches of newly
+        # page-locked host memory)
+        for s, w, h in zip(sims, cases, sdf_host):
+            s.init(h, w.c1_tilde, w.c2_tilde)
+        b.step(max(3, args.warmup))
+        for s, o in zip(sims, outs):
+            s.fields(names=names, dtype="f32", out=o.numpy())
         barrier()
         torch.cuda.synchronize(dev)
         t0 = torch.cuda.Event(enable_timing=True)

@@ -107,11 +107,16 @@ lbm::Coeffs<R> coeffs_of(const lbm_params* p) {
     return C;
 }
 
+// two_over_W = 2 / W, taken once on the host: an FP64 division per node would
+// cost more than the kernel's memory traffic
 __global__ void sdf_to_fields_kernel(const double* __restrict__ sdf, double* phi, double* c1, double* c2,
-                                     size_t n, double W, double c1t, double c2t) {
+                                     size_t n, double two_over_W, double c1t, double c2t) {
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const double l = sdf[k];
-        const double ph = 0.5 + 0.5 * tanh(2.0 * l / W);  // Eq. (2)
+        const double a = sdf[k] * two_over_W;
+        // Eq. (2).  tanh saturates: for |a| >= 20, 1 - |tanh a| < 1e-17, below half
+        // the spacing of doubles under 1, so the rounded profile is exactly 0 or 1
+        // there, and only the interface band pays for the FP64 tanh
+        const double ph = fabs(a) >= 20.0 ? (a > 0.0 ? 1.0 : 0.0) : 0.5 + 0.5 * tanh(a);
         phi[k] = ph;
         c1[k] = c1t * ph;
         c2[k] = c2t * (1.0 - ph);
@@ -124,7 +129,7 @@ namespace lbm {
 cudaError_t launch_sdf_to_fields(const double* sdf, double* phi, double* c1, double* c2, size_t n,
                                  double W, double c1t, double c2t, cudaStream_t s) {
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-    sdf_to_fields_kernel<<<blocks, 256, 0, s>>>(sdf, phi, c1, c2, n, W, c1t, c2t);
+    sdf_to_fields_kernel<<<blocks, 256, 0, s>>>(sdf, phi, c1, c2, n, 2.0 / W, c1t, c2t);
     return cudaGetLastError();
 }
 }  // namespace lbm

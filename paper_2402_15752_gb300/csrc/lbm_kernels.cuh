@@ -1459,9 +1459,12 @@ __global__ void init_kernel(InitFields in, T* __restrict__ pop, R* __restrict__ 
         long long rest = Phi;
         for (int i = 1; i < 9; ++i) {
             const R w = w9<R>(i);
-            const long long Fi = llrint(double(w * phi * (R(1) + R(3) * cu_of(i)) - R(0.5) * w) * 2147483648.0);
+            // the FP32 value times 2^31 (exact) rounded to the nearest integer, ties
+            // to even: the integer a double llrint gives, without FP64 arithmetic
+            // (the values stay below 1 in magnitude for |u| below the lattice speed)
+            const int Fi = __float2int_rn((w * phi * (R(1) + R(3) * cu_of(i)) - R(0.5) * w) * 2147483648.0f);
             rest -= Fi;
-            fp[pull_off<NQ>(g, x, y, 0, i)] = (int)Fi;
+            fp[pull_off<NQ>(g, x, y, 0, i)] = Fi;
         }
         fp[pull_off<NQ>(g, x, y, 0, 0)] = (int)rest;
     } else if constexpr (IsHalf<T>::value) {
