@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--cases", type=int, default=256, help="batched256: number of lattices (a smaller "
                     "sample of the same generator, for profiling)")
     ap.add_argument("--tiling", default=None, help="batched256: tile WxH instead of the autotuner's choice")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short measurements of the other workloads that the default run "
+                    "adds to its line (N = 1 only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -353,6 +356,10 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, 256 * 512, args.workload + " scaled to")
+    others = None
+    if (world == 1 and not args.no_secondary and args.workload == "bubble1024x2048"
+            and args.precision == "fp32"):
+        others = secondary(dev)
 
     if rank == 0:
         line = {
@@ -372,12 +379,82 @@ def run_ours(args, rank, world, local):
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if others is not None:
+            line["secondary"] = others
         if not state_ok:
             line["failed"] = "the state went non-finite during the timed steps"
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def timed_steps(step, stream, steps, warmup):
+    """CUDA-event milliseconds of `steps` calls' worth of step(n), after warm-up."""
+    import torch
+    step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def secondary(dev):
+    """Short measurements of the other workloads, outside the timed region of the
+    line's own number: the 8192 x 8192 droplets (FP32), the bubble in bfloat16
+    storage, and the 256 batched droplets (autotuned tiles).  Each: node updates
+    per second over a fixed number of steps after 5 warm-up steps, and the
+    fraction of the measured copy bandwidth at its algorithmic bytes per node."""
+    from paper_2402_15752_gb300 import Batch, Simulation
+    from paper_2402_15752_gb300 import workloads as wl
+
+    peak, _ = hbm_peak()
+    out = {}
+
+    def entry(cells, steps, ms, bpc, **extra):
+        mlups = cells * steps / (ms * 1e-3) / 1e6
+        return dict(value=mlups, unit="MLUPS", steps=steps, ms_per_step=ms / steps, bytes_per_cell=bpc,
+                    frac=bpc * mlups * 1e6 / 1e9 / peak, **extra)
+
+    for name, prec, steps, bpc in (("droplets8192", "fp32", 100, 264), ("bubble1024x2048", "bf16", 2000, 176)):
+        key = "%s_%s" % (name, prec)
+        sim = None
+        try:
+            w = wl.get(name)
+            sim = Simulation(w.params, precision=prec, device=dev)
+            sim.init(w.sdf, w.c1_tilde, w.c2_tilde)
+            ms = timed_steps(sim.step, sim.stream, steps, 5)
+            sim.sync()
+            out[key] = entry(w.cells, steps, ms, bpc)
+        except Exception as e:  # reported in the line; the line's own number stands
+            out[key] = {"failed": str(e)[:200]}
+        finally:
+            if sim is not None:
+                sim.close()
+    sims, b = [], None
+    try:
+        cases = wl.batched()
+        sims = [Simulation(w.params, precision="fp32", device=dev) for w in cases]
+        for sm, w in zip(sims, cases):
+            sm.init(w.sdf, w.c1_tilde, w.c2_tilde)
+        b = Batch(sims)
+        tune = b.autotune(steps_per_trial=10)
+        ms = timed_steps(b.step, sims[0].stream, 200, 5)
+        b.sync()
+        out["batched256_fp32"] = entry(sum(w.cells for w in cases), 200, ms, 264, cases=len(cases),
+                                       tiling={k: tune[k] for k in ("tile_w", "tile_h")})
+    except Exception as e:
+        out["batched256_fp32"] = {"failed": str(e)[:200]}
+    finally:
+        if b is not None:
+            b.close()
+        for sm in sims:
+            sm.close()
+    return out
 
 
 def run_batched(args, rank, world, local):
