@@ -143,6 +143,27 @@ def test_init_from_device_fields():
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("W", [4.0, 5.0])
+def test_init_profile_from_the_signed_distance(W):
+    """lbm_init's profile phi = 1/2 + 1/2 tanh(2 l / W) (Eq. 2), c1 = c1~ phi,
+    c2 = c2~ (1 - phi), read back before any step in FP64 storage, against
+    numpy's FP64 tanh: across the interface band and the saturated bulk on both
+    sides (|2 l / W| up to 24; beyond 20 the kernel skips the tanh, whose
+    rounded value is +-1 there), to the rounding of the moments."""
+    nx, ny = 160, 4
+    l = np.tile((np.arange(nx) - 80.0) * 0.75, (ny, 1))
+    p = dict(wl.BASE, nx=nx, ny=ny, W=W)
+    sim = Simulation(p, precision="fp64")
+    sim.init(l, 0.7, 0.2)
+    f = sim.fields(names=("phi", "c1", "c2"))
+    phi = 0.5 + 0.5 * np.tanh(2.0 * l / W)
+    assert np.abs(2.0 * l / W).max() > 23 and (np.abs(2.0 * l / W) < 20).sum() > 40
+    assert np.abs(f["phi"] - phi).max() < 2e-15
+    assert np.abs(f["c1"] - 0.7 * phi).max() < 2e-15
+    assert np.abs(f["c2"] - 0.2 * (1.0 - phi)).max() < 2e-15
+    sim.close()
+
+
 def test_nonfinite_state_is_reported():
     w = wl.droplet64(nx=32, ny=32, R=8.0)
     sim = Simulation(w.params, precision="fp32")
