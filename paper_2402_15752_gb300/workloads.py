@@ -128,7 +128,13 @@ def planar1024(nx=1024, ny=8, x0=None, steps=20000, **over) -> Workload:
 
 
 def bubble1024x2048(nx=1024, ny=2048, R=None, steps=10000, **over) -> Workload:
-    """Rising bubble; smaller boxes keep the geometry in proportion."""
+    """Rising bubble; smaller boxes keep the geometry in proportion.
+
+    Defined for 10 000 steps.  At full size it goes non-finite between 13 000
+    and 14 000 steps, in FP64 and FP32 alike: c1 + c2 builds up on the gas side
+    of the bubble's lower interface (to 6.6 by then), and mu_lin exp(-beta T)
+    takes tau_g there toward 1/2.  visc_beta=0 (or visc_model=0) runs 30 000
+    steps."""
     R = 128.0 * nx / 1024 if R is None else R
     beta = float(rng(WORKLOAD_INDEX["bubble1024x2048"]).uniform(0.0, 2.0))
     p = dict(BASE, nx=nx, ny=ny, wall_x=1, wall_y=1, sigma=0.01,
